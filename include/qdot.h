@@ -1,0 +1,169 @@
+/*
+ * qdot -- error-bounded quantized dot product on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of libqdot.so.  Every entry point takes plain pointers and sizes; the
+ * caller owns all memory (device buffers, workspace, streams) and the library
+ * allocates nothing on any path below.  Device results are written to device
+ * memory, asynchronously on the caller's stream, so calls can be recorded in
+ * CUDA graphs; a host wrapper copies them back when it needs them.
+ *
+ * The method is that of Diffenderfer, Osei-Kuffuor and Menon, "Qdot:
+ * Quantized Dot Product Kernel for Approximate High Performance Computing"
+ * (arXiv 2105.00115): Algorithm 2 (parameter selection: exponent keys, bins,
+ * bin scores eq. bin-score-def, precisions eq. precision-def) followed by
+ * Algorithm 1 (computation phase), i.e. Algorithm 3.
+ *
+ * Definitions used throughout (the paper's notation):
+ *   e(v)      unbiased IEEE exponent of a finite nonzero double v (floor(log2|v|),
+ *             subnormals with their true exponent) -- Sec. 1.1 flexp.
+ *   e_i       e(x_i) + e(y_i), the key of component i -- Algorithm 2, exponent
+ *             preprocessing.  Components with x_i == 0 or y_i == 0 are class ZERO:
+ *             they belong to no bin and contribute exactly 0.
+ *   bins      block == 0: exact binning, one bin per distinct key (Sec. 3.2);
+ *             block == B: the non-ZERO components of each index block
+ *             [bB, (b+1)B), u_b = max key, M_b = count (Sec. 5, blocked approach).
+ *   f         floor(log2(eps / N_bins)) (split_budget = 1, Sec. 4.1) or
+ *             floor(log2 eps) (split_budget = 0), computed exactly.
+ *   sigma_k   ceil(log2 M_k) + u_k - e_max - f + 1 (eq. bin-score-def).
+ *   class     sigma < 0: PERF; < m_half: HALF; < m_single: SINGLE; else DOUBLE
+ *             (eq. precision-def; m_half, m_single = 10, 23, or 11, 24 when
+ *             mant_reading = 1).
+ *   q(v)      v with its significand rounded to 11 (HALF) or 24 (SINGLE) bits,
+ *             ties to even, exponent unbounded (Sec. 3.2 scale / cast / rescale);
+ *             q(v) = v for DOUBLE, 0 for PERF and ZERO.
+ *   z         sum_i q(x_i) q(y_i), evaluated with exact integer arithmetic and
+ *             rounded once to the nearest double (exact up to a truncation of at
+ *             most n 2^(e_max - 97) for n <= 2^28; see qdot()).
+ *
+ * Errors: every entry point returns a qdot_status.  Argument errors are
+ * detected on the host before anything is launched (nothing is written).  Data
+ * errors found on the device (a NaN or Inf component) are reported in the
+ * `status` field of the device result; the host call still returns QDOT_OK.
+ * qdot_last_error() gives a message for the last failing call on this thread.
+ */
+#ifndef QDOT_H
+#define QDOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QDOT_OK = 0,
+  QDOT_ERR_ARG = 1,        /* invalid argument (checked on the host) */
+  QDOT_ERR_NONFINITE = 2,  /* a component of x or y is NaN or Inf (device status) */
+  QDOT_ERR_CUDA = 3,       /* a CUDA runtime call failed; see qdot_last_error() */
+  QDOT_ERR_TIMEOUT = 4,    /* a bounded device wait expired (device status) */
+  QDOT_ERR_WORKSPACE = 5,  /* workspace missing, misaligned or too small */
+  QDOT_ERR_NOCONV = 6      /* an iterative solver hit its iteration cap */
+} qdot_status;
+
+enum { QDOT_PERF = 0, QDOT_HALF = 1, QDOT_SINGLE = 2, QDOT_DOUBLE = 3, QDOT_ZERO = 4 };
+
+/* Key range: every e_i and every block key ceil(log2 M_b) + u_b lies in
+ * [QDOT_KEY_MIN, QDOT_KEY_MIN + QDOT_KEY_COUNT). */
+#define QDOT_KEY_MIN (-2148)
+#define QDOT_KEY_COUNT 4224
+
+/* Execution path for qdot(): chosen automatically unless forced. */
+enum { QDOT_PATH_AUTO = 0, QDOT_PATH_TWO_PASS = 1, QDOT_PATH_ONE_PASS = 2 };
+
+typedef struct {
+  double eps;           /* qdot tolerance eps > 0, finite (Algorithm 3 input) */
+  int32_t block;        /* 0: exact binning; else B, a power of two in [1, 2^20] */
+  int32_t split_budget; /* 1: eps / N_bins (default, Sec. 4.1); 0: eps (eq. bin-score-def) */
+  int32_t mant_reading; /* 0: m_half, m_single = 10, 23 (default); 1: 11, 24 */
+  int32_t path;         /* QDOT_PATH_*; the one-pass path needs 32 <= B <= 256 */
+} qdot_params;
+
+/* Device-side result of one qdot (80 bytes). */
+typedef struct {
+  double value;     /* z */
+  double bound;     /* a-priori absolute error bound N_bins 2^(e_max + f) (<= eps 2^e_max) */
+  int64_t n_bins;   /* number of non-empty bins N_bins */
+  int64_t count[5]; /* components per class PERF, HALF, SINGLE, DOUBLE, ZERO */
+  int32_t e_max;    /* max key over non-ZERO components (0 if none) */
+  int32_t e_min;    /* min key over non-ZERO components (0 if none) */
+  int32_t f;        /* floor(log2 eps_eff) used in the scores */
+  int32_t status;   /* QDOT_OK or QDOT_ERR_NONFINITE */
+} qdot_result;
+
+/* The parameter selection of one call (Algorithm 2 output), compact form:
+ * the class of every key.  For block == 0 the key is e_i; for block == B it
+ * is the block key ceil(log2 M_b) + u_b.  4264 bytes. */
+typedef struct {
+  int32_t e_max, e_min, f, status;
+  int64_t n_bins;
+  int32_t block, key_min;               /* key_min == QDOT_KEY_MIN */
+  int32_t m_half, m_single;
+  int32_t reserved[2];
+  uint8_t cls[QDOT_KEY_COUNT];          /* class per key, index key - key_min */
+} qdot_selection;
+
+/* CSR matrix in device memory (rows sorted, int64 row pointers). */
+typedef struct {
+  int64_t n;              /* rows == columns */
+  int64_t nnz;
+  const int64_t* rowptr;  /* [n + 1] */
+  const int32_t* col;     /* [nnz] */
+  const double* val;      /* [nnz] */
+} qdot_csr;
+
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace qdot() / qdot_explain() need for n components
+ * with parameters p (0 on invalid arguments).  The workspace is scratch: its
+ * contents on entry are ignored and on exit undefined. */
+size_t qdot_workspace_size(int64_t n, const qdot_params* p);
+
+/* z = qdot(x, y, eps) -- Algorithm 3 of the paper.
+ *   x, y     device pointers to n doubles (8-byte aligned; 16-byte alignment
+ *            selects 128-bit loads).  May be NULL when n == 0.
+ *   p        host pointer to the parameters (read during the call).
+ *   out      device pointer to one qdot_result (written asynchronously).
+ *   sel      optional device pointer to a qdot_selection receiving the
+ *            parameter selection (for qdot_backward); NULL to skip.
+ *   ws       device workspace of at least qdot_workspace_size(n, p) bytes,
+ *            256-byte aligned.
+ *   stream   cudaStream_t (NULL = legacy default stream).
+ * Returns QDOT_ERR_ARG / QDOT_ERR_WORKSPACE on bad arguments (nothing is
+ * launched), QDOT_ERR_CUDA if a launch fails, else QDOT_OK. */
+qdot_status qdot(const double* x, const double* y, int64_t n, const qdot_params* p, qdot_result* out,
+                 qdot_selection* sel, void* ws, size_t ws_bytes, void* stream);
+
+/* qdot() that also writes, per component i, its class (cls[i], uint8) and
+ * the quantized values q(x_i), q(y_i) (0 for PERF and ZERO; a quantized value
+ * that overflows double is written as +-Inf).  Any of cls, qx, qy may be
+ * NULL.  Uses the two-pass path. */
+qdot_status qdot_explain(const double* x, const double* y, int64_t n, const qdot_params* p, qdot_result* out,
+                         uint8_t* cls, double* qx, double* qy, void* ws, size_t ws_bytes, void* stream);
+
+/* Plain FP64 dot product x.y (the comparator of the paper's speedup metric,
+ * eq. approx-speedup): fused multiply-adds in a fixed order, written to
+ * *out (device).  Workspace: qdot_dot_fp64_workspace_size(). */
+size_t qdot_dot_fp64_workspace_size(void);
+qdot_status qdot_dot_fp64(const double* x, const double* y, int64_t n, double* out, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* End-to-end call from host buffers: copies x_host, y_host (n doubles each,
+ * preferably pinned) into the caller's device buffers x_dev, y_dev, runs
+ * qdot() on them, and copies the result into *out_host.  Synchronises the
+ * stream before returning. */
+qdot_status qdot_from_host(const double* x_host, const double* y_host, int64_t n, const qdot_params* p,
+                           qdot_result* out_host, double* x_dev, double* y_dev, qdot_result* out_dev, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/* Message for the last failing call on the calling thread ("" if none). */
+const char* qdot_last_error(void);
+
+/* Library version string. */
+const char* qdot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDOT_H */

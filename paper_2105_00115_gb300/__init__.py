@@ -1,0 +1,169 @@
+"""qdot on one GB300: Python binding of libqdot.so.
+
+Thin marshalling layer over the C ABI in include/qdot.h: every step of the
+method runs in the library's CUDA kernels; PyTorch only provides device
+memory (tensors, workspaces) and streams.  There is no CPU fallback: if the
+library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _abi
+from ._abi import Params, QdotError, Result, Selection, check, load
+
+__all__ = ["QdotResult", "QdotError", "qdot", "qdot_async", "explain", "dot_fp64", "from_host", "workspace_size",
+           "load", "params", "decode_result"]
+
+CLASS_NAMES = ("perforate", "half", "single", "double", "zero")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+@dataclass
+class QdotResult:
+    value: float
+    bound: float
+    n_bins: int
+    count: tuple
+    e_max: int
+    e_min: int
+    f: int
+    status: int
+
+
+def params(eps=1e-16, block=32, split_budget=1, mant_reading=0, path="auto") -> Params:
+    return Params(float(eps), int(block), int(split_budget), int(mant_reading), _abi.PATHS[path])
+
+
+def decode_result(buf) -> QdotResult:
+    """Parse an 80-byte qdot_result (host bytes / numpy / CPU tensor)."""
+    raw = bytes(np.asarray(buf, dtype=np.uint8).tobytes())
+    r = Result.from_buffer_copy(raw[: ctypes.sizeof(Result)])
+    return QdotResult(r.value, r.bound, r.n_bins, tuple(r.count), r.e_max, r.e_min, r.f, r.status)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_vec(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float64 or t.dim() != 1:
+        raise TypeError(f"{name} must be a 1-D float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def workspace_size(n: int, p: Params) -> int:
+    return int(load().qdot_workspace_size(int(n), ctypes.byref(p)))
+
+
+def _workspace(nbytes, device, ws=None):
+    torch = _torch()
+    nbytes = max(int(nbytes), 256)
+    if ws is not None and ws.numel() >= nbytes:
+        return ws
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def qdot_async(x, y, eps=1e-16, block=32, split_budget=1, mant_reading=0, path="auto", out=None, ws=None,
+               selection=None, stream=None):
+    """Launch qdot(x, y) on ``stream``; returns the 80-byte device result tensor.
+    ``selection`` (uint8 CUDA tensor of sizeof(qdot_selection) bytes) receives
+    the parameter selection when given."""
+    torch = _torch()
+    lib = load()
+    _check_vec(x, "x")
+    _check_vec(y, "y")
+    if x.numel() != y.numel():
+        raise ValueError("x and y must have the same length")
+    p = params(eps, block, split_budget, mant_reading, path)
+    n = x.numel()
+    need = lib.qdot_workspace_size(n, ctypes.byref(p))
+    if need == 0:
+        raise QdotError(1, "invalid qdot parameters")
+    ws = _workspace(need, x.device, ws)
+    if out is None:
+        out = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=x.device)
+    st = lib.qdot(_ptr(x), _ptr(y), n, ctypes.byref(p), _ptr(out), _ptr(selection), _ptr(ws), ws.numel(),
+                  _stream_ptr(stream))
+    check(st, lib)
+    return out
+
+
+def qdot(x, y, eps=1e-16, block=32, split_budget=1, mant_reading=0, path="auto", stream=None) -> QdotResult:
+    """qdot(x, y, eps) on the GPU (Algorithm 3); synchronises and returns the result."""
+    out = qdot_async(x, y, eps, block, split_budget, mant_reading, path, stream=stream)
+    r = decode_result(out.cpu().numpy())
+    if r.status != 0:
+        raise QdotError(r.status, "non-finite component in x or y")
+    return r
+
+
+def explain(x, y, eps=1e-16, block=32, split_budget=1, mant_reading=0, stream=None):
+    """qdot plus the per-component class map and quantized vectors (device tensors)."""
+    torch = _torch()
+    lib = load()
+    _check_vec(x, "x")
+    _check_vec(y, "y")
+    p = params(eps, block, split_budget, mant_reading, "two_pass")
+    n = x.numel()
+    need = lib.qdot_workspace_size(n, ctypes.byref(p))
+    if need == 0:
+        raise QdotError(1, "invalid qdot parameters")
+    ws = _workspace(need, x.device)
+    out = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=x.device)
+    cls = torch.empty(n, dtype=torch.uint8, device=x.device)
+    qx = torch.empty(n, dtype=torch.float64, device=x.device)
+    qy = torch.empty(n, dtype=torch.float64, device=x.device)
+    st = lib.qdot_explain(_ptr(x), _ptr(y), n, ctypes.byref(p), _ptr(out), _ptr(cls), _ptr(qx), _ptr(qy),
+                          _ptr(ws), ws.numel(), _stream_ptr(stream))
+    check(st, lib)
+    return decode_result(out.cpu().numpy()), cls, qx, qy
+
+
+def dot_fp64(x, y, stream=None) -> float:
+    """Plain FP64 dot product on the GPU (the speedup comparator)."""
+    torch = _torch()
+    lib = load()
+    _check_vec(x, "x")
+    _check_vec(y, "y")
+    ws = _workspace(lib.qdot_dot_fp64_workspace_size(), x.device)
+    out = torch.empty(1, dtype=torch.float64, device=x.device)
+    check(lib.qdot_dot_fp64(_ptr(x), _ptr(y), x.numel(), _ptr(out), _ptr(ws), ws.numel(), _stream_ptr(stream)), lib)
+    return float(out.item())
+
+
+def from_host(x_host, y_host, eps=1e-16, block=32, split_budget=1, mant_reading=0, path="auto", x_dev=None,
+              y_dev=None, ws=None, stream=None) -> QdotResult:
+    """End-to-end qdot from host tensors (pinned CPU float64): copies in, runs, copies the result out."""
+    torch = _torch()
+    lib = load()
+    n = x_host.numel()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if x_dev is None:
+        x_dev = torch.empty(n, dtype=torch.float64, device=dev)
+    if y_dev is None:
+        y_dev = torch.empty(n, dtype=torch.float64, device=dev)
+    p = params(eps, block, split_budget, mant_reading, path)
+    ws = _workspace(lib.qdot_workspace_size(n, ctypes.byref(p)), dev, ws)
+    out_dev = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=dev)
+    res = Result()
+    st = lib.qdot_from_host(ctypes.c_void_p(x_host.data_ptr()), ctypes.c_void_p(y_host.data_ptr()), n,
+                            ctypes.byref(p), ctypes.byref(res), _ptr(x_dev), _ptr(y_dev), _ptr(out_dev), _ptr(ws),
+                            ws.numel(), _stream_ptr(stream))
+    check(st, lib)
+    return QdotResult(res.value, res.bound, res.n_bins, tuple(res.count), res.e_max, res.e_min, res.f, res.status)

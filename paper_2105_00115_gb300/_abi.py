@@ -1,0 +1,91 @@
+"""ctypes view of include/qdot.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqdot.so")
+
+KEY_MIN = -2148
+KEY_COUNT = 4224
+PATHS = {"auto": 0, "two_pass": 1, "one_pass": 2}
+STATUS = {0: "QDOT_OK", 1: "QDOT_ERR_ARG", 2: "QDOT_ERR_NONFINITE", 3: "QDOT_ERR_CUDA", 4: "QDOT_ERR_TIMEOUT",
+          5: "QDOT_ERR_WORKSPACE", 6: "QDOT_ERR_NOCONV"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("block", ctypes.c_int32), ("split_budget", ctypes.c_int32),
+                ("mant_reading", ctypes.c_int32), ("path", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("value", ctypes.c_double), ("bound", ctypes.c_double), ("n_bins", ctypes.c_int64),
+                ("count", ctypes.c_int64 * 5), ("e_max", ctypes.c_int32), ("e_min", ctypes.c_int32),
+                ("f", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class Selection(ctypes.Structure):
+    _fields_ = [("e_max", ctypes.c_int32), ("e_min", ctypes.c_int32), ("f", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("n_bins", ctypes.c_int64), ("block", ctypes.c_int32),
+                ("key_min", ctypes.c_int32), ("m_half", ctypes.c_int32), ("m_single", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2), ("cls", ctypes.c_uint8 * KEY_COUNT)]
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+assert ctypes.sizeof(Result) == 80
+assert ctypes.sizeof(Params) == 24
+
+# (name, restype, argtypes) for every entry point of include/qdot.h
+_VP = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+_PP = ctypes.POINTER(Params)
+SIGNATURES = {
+    "qdot_workspace_size": (_SZ, [_I64, _PP]),
+    "qdot": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _SZ, _VP]),
+    "qdot_explain": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "qdot_dot_fp64_workspace_size": (_SZ, []),
+    "qdot_dot_fp64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
+    "qdot_from_host": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "qdot_last_error": (ctypes.c_char_p, []),
+    "qdot_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class QdotError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libqdot.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_2105_00115_gb300.build.build() "
+                              "(the qdot path has no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(status: int, lib=None) -> None:
+    if status != 0:
+        lib = lib or load()
+        raise QdotError(status, lib.qdot_last_error().decode())

@@ -1,0 +1,236 @@
+// C ABI of libqdot.so: argument checks, workspace planning, path choice.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "qdot_common.cuh"
+#include "qdot_internal.h"
+
+namespace qd {
+
+static thread_local std::string g_error;
+void set_error(const std::string& msg) { g_error = msg; }
+void clear_error() { g_error.clear(); }
+
+const DeviceInfo& device_info() {
+  static std::mutex mu;
+  static DeviceInfo cache[64];
+  static bool filled[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    static DeviceInfo none;
+    return none;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!filled[dev]) {
+    DeviceInfo di;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) di.sms = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+      di.max_smem_optin = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) == cudaSuccess) di.l2_bytes = (size_t)v;
+    cudaGetLastError();
+    cache[dev] = di;
+    filled[dev] = true;
+  }
+  return cache[dev];
+}
+
+bool valid_params(int64_t n, const qdot_params* p, std::string* why) {
+  if (!p) {
+    *why = "params pointer is NULL";
+    return false;
+  }
+  if (n < 0) {
+    *why = "n must be >= 0";
+    return false;
+  }
+  if (!(p->eps > 0.0) || !std::isfinite(p->eps)) {
+    *why = "eps must be a finite number > 0";
+    return false;
+  }
+  if (p->block < 0 || p->block > (1 << 20) || (p->block & (p->block - 1)) != 0) {
+    *why = "block must be 0 (exact binning) or a power of two in [1, 2^20]";
+    return false;
+  }
+  if (p->split_budget != 0 && p->split_budget != 1) {
+    *why = "split_budget must be 0 or 1";
+    return false;
+  }
+  if (p->mant_reading != 0 && p->mant_reading != 1) {
+    *why = "mant_reading must be 0 or 1";
+    return false;
+  }
+  if (p->path < QDOT_PATH_AUTO || p->path > QDOT_PATH_ONE_PASS) {
+    *why = "path must be QDOT_PATH_AUTO, QDOT_PATH_TWO_PASS or QDOT_PATH_ONE_PASS";
+    return false;
+  }
+  return true;
+}
+
+static bool aligned16(const void* a, const void* b) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0;
+}
+
+}  // namespace qd
+
+using namespace qd;
+
+namespace {
+
+enum PathChoice { kTwoPass, kOnePass };
+
+PathChoice choose_path(int64_t n, const qdot_params* p, bool al16) {
+  if (p->path == QDOT_PATH_TWO_PASS) return kTwoPass;
+  bool ok = one_pass_supported(n, p, al16);
+  if (p->path == QDOT_PATH_ONE_PASS) return ok ? kOnePass : kTwoPass;
+  return ok ? kOnePass : kTwoPass;
+}
+
+size_t workspace_for(int64_t n, const qdot_params* p, bool al16, PathChoice* choice) {
+  PathChoice c = choose_path(n, p, al16);
+  if (choice) *choice = c;
+  if (c == kOnePass) return plan_one_pass(n, p).total;
+  return plan_two_pass(n, p, al16).total;
+}
+
+qdot_status check_common(const double* x, const double* y, int64_t n, const qdot_params* p, const void* out,
+                         const void* ws) {
+  std::string why;
+  if (!valid_params(n, p, &why)) {
+    set_error("qdot: " + why);
+    return QDOT_ERR_ARG;
+  }
+  if (n > 0 && (!x || !y)) {
+    set_error("qdot: x and y must be non-NULL when n > 0");
+    return QDOT_ERR_ARG;
+  }
+  if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 7u) != 0) {
+    set_error("qdot: x and y must be 8-byte aligned");
+    return QDOT_ERR_ARG;
+  }
+  if (!out) {
+    set_error("qdot: out must be a device pointer to a qdot_result");
+    return QDOT_ERR_ARG;
+  }
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) {
+    set_error("qdot: workspace must be non-NULL and 256-byte aligned");
+    return QDOT_ERR_WORKSPACE;
+  }
+  return QDOT_OK;
+}
+
+qdot_status cuda_fail(const char* what, cudaError_t e) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return QDOT_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qdot_workspace_size(int64_t n, const qdot_params* p) {
+  std::string why;
+  if (!valid_params(n, p, &why)) return 0;
+  // Size for the larger of the two alignment cases so any pointer fits.
+  return std::max(workspace_for(n, p, true, nullptr), workspace_for(n, p, false, nullptr));
+}
+
+qdot_status qdot(const double* x, const double* y, int64_t n, const qdot_params* p, qdot_result* out,
+                 qdot_selection* sel, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  qdot_status s = check_common(x, y, n, p, out, ws);
+  if (s != QDOT_OK) return s;
+  const bool al16 = aligned16(x, y);
+  PathChoice c;
+  size_t need = workspace_for(n, p, al16, &c);
+  if (ws_bytes < need) {
+    set_error("qdot: workspace too small (" + std::to_string(ws_bytes) + " < " + std::to_string(need) + ")");
+    return QDOT_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (c == kOnePass)
+    e = launch_one_pass(x, y, n, p, plan_one_pass(n, p), ws, out, sel, st);
+  else
+    e = launch_two_pass(x, y, n, p, plan_two_pass(n, p, al16), ws, out, sel, nullptr, nullptr, nullptr, st);
+  if (e != cudaSuccess) return cuda_fail("qdot launch", e);
+  return QDOT_OK;
+}
+
+qdot_status qdot_explain(const double* x, const double* y, int64_t n, const qdot_params* p, qdot_result* out,
+                         uint8_t* cls, double* qx, double* qy, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  qdot_status s = check_common(x, y, n, p, out, ws);
+  if (s != QDOT_OK) return s;
+  const bool al16 = aligned16(x, y);
+  TwoPassPlan pl = plan_two_pass(n, p, al16);
+  if (ws_bytes < pl.total) {
+    set_error("qdot_explain: workspace too small (" + std::to_string(ws_bytes) + " < " + std::to_string(pl.total) +
+              ")");
+    return QDOT_ERR_WORKSPACE;
+  }
+  // The explain kernel writes every valid component; a NULL output is skipped.
+  cudaError_t e = launch_two_pass(x, y, n, p, pl, ws, out, nullptr, cls, qx, qy, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail("qdot_explain launch", e);
+  return QDOT_OK;
+}
+
+size_t qdot_dot_fp64_workspace_size(void) { return dot_fp64_workspace(); }
+
+qdot_status qdot_dot_fp64(const double* x, const double* y, int64_t n, double* out, void* ws, size_t ws_bytes,
+                          void* stream) {
+  clear_error();
+  if (n < 0 || (n > 0 && (!x || !y)) || !out) {
+    set_error("qdot_dot_fp64: invalid arguments");
+    return QDOT_ERR_ARG;
+  }
+  if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 7u) != 0) {
+    set_error("qdot_dot_fp64: x and y must be 8-byte aligned");
+    return QDOT_ERR_ARG;
+  }
+  if (!ws || ws_bytes < dot_fp64_workspace() || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0) {
+    set_error("qdot_dot_fp64: workspace missing, misaligned or too small");
+    return QDOT_ERR_WORKSPACE;
+  }
+  cudaError_t e = launch_dot_fp64(x, y, n, out, ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail("qdot_dot_fp64 launch", e);
+  return QDOT_OK;
+}
+
+qdot_status qdot_from_host(const double* x_host, const double* y_host, int64_t n, const qdot_params* p,
+                           qdot_result* out_host, double* x_dev, double* y_dev, qdot_result* out_dev, void* ws,
+                           size_t ws_bytes, void* stream) {
+  clear_error();
+  if (n > 0 && (!x_host || !y_host)) {
+    set_error("qdot_from_host: host buffers must be non-NULL when n > 0");
+    return QDOT_ERR_ARG;
+  }
+  if (!out_host) {
+    set_error("qdot_from_host: out_host must be non-NULL");
+    return QDOT_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (n > 0) {
+    e = cudaMemcpyAsync(x_dev, x_host, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail("qdot_from_host: copy of x", e);
+    e = cudaMemcpyAsync(y_dev, y_host, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail("qdot_from_host: copy of y", e);
+  }
+  qdot_status s = qdot(x_dev, y_dev, n, p, out_dev, nullptr, ws, ws_bytes, stream);
+  if (s != QDOT_OK) return s;
+  e = cudaMemcpyAsync(out_host, out_dev, sizeof(qdot_result), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail("qdot_from_host: copy of the result", e);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("qdot_from_host: synchronize", e);
+  return QDOT_OK;
+}
+
+const char* qdot_last_error(void) { return g_error.c_str(); }
+
+const char* qdot_version(void) { return "qdot-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Host-side plumbing shared by the translation units of libqdot.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "qdot.h"
+
+namespace qd {
+
+// Thread-local error message behind qdot_last_error().
+void set_error(const std::string& msg);
+void clear_error();
+
+// Device facts cached per device ordinal.
+struct DeviceInfo {
+  int sms = 0;
+  int max_smem_optin = 0;
+  size_t l2_bytes = 0;
+};
+const DeviceInfo& device_info();
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Execution modes of the two-pass path.
+enum Mode { kModeExact = 0, kModeBlock1 = 1, kModeBlockSmall = 2, kModeBlockLarge = 3 };
+
+// Workspace plan of the two-pass path for one call.
+struct TwoPassPlan {
+  int mode = 0;
+  int vec = 2;          // 2: 128-bit loads (16-byte aligned x, y), 1: 64-bit loads
+  int log2b = 0;        // log2(block) for block >= 1
+  int grid_stats = 0;
+  int grid_apply = 0;
+  long long nblocks = 0;
+  size_t off_sel = 0, off_hdr = 0, off_stats = 0, off_apply = 0, off_hist = 0, off_keys = 0;
+  size_t total = 0;
+};
+
+bool valid_params(int64_t n, const qdot_params* p, std::string* why);
+TwoPassPlan plan_two_pass(int64_t n, const qdot_params* p, bool aligned16);
+
+// Launch the two-pass sequence (stats -> select -> apply [or explain] ->
+// final).  Returns cudaSuccess or the first launch error.
+cudaError_t launch_two_pass(const double* x, const double* y, int64_t n, const qdot_params* p,
+                            const TwoPassPlan& plan, void* ws, qdot_result* out, qdot_selection* sel,
+                            uint8_t* cls, double* qx, double* qy, cudaStream_t stream);
+
+// One-pass (deferred selection) path for 32 <= block <= 256.
+struct OnePassPlan {
+  int log2b = 0;
+  int grid = 0;
+  int window = 0;         // keys kept per record
+  long long units = 0;    // work units (each produces one record)
+  long long unit_blocks = 0;
+  size_t off_sel = 0, off_hdr = 0, off_rec = 0, off_misc = 0;
+  size_t rec_bytes = 0;
+  size_t total = 0;
+};
+bool one_pass_supported(int64_t n, const qdot_params* p, bool aligned16);
+OnePassPlan plan_one_pass(int64_t n, const qdot_params* p);
+cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const qdot_params* p,
+                            const OnePassPlan& plan, void* ws, qdot_result* out, qdot_selection* sel,
+                            cudaStream_t stream);
+
+// Plain FP64 dot.
+cudaError_t launch_dot_fp64(const double* x, const double* y, int64_t n, double* out, void* ws,
+                            cudaStream_t stream);
+size_t dot_fp64_workspace();
+
+}  // namespace qd

@@ -1,0 +1,186 @@
+"""GPU parity of qdot (C ABI through the Python binding) against the CPU oracle.
+
+Bar (spec tolerance): class map, quantized values, class counts, e_max,
+e_min, N_bins and f bit-exact; z within 1e-13 * sum_i |x_i y_i| (the exact
+sum of absolute products, from the oracle).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from golden_cases import load_cases
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_00115_gb300 import build as qbuild
+    qbuild.build()
+    import paper_2105_00115_gb300 as qq
+    qq.load()
+    return qq
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _same_bits(a, b):
+    return np.array_equal(np.asarray(a).view(np.int64), np.asarray(b).view(np.int64))
+
+
+def _check(q, orc, x, y, eps, block, split=1, mant=0, explain=True, path="auto"):
+    ref = orc.qdot(x, y, eps=eps, block=block, split_budget=split, mant_reading=mant, explain=explain)
+    xd, yd = _dev(x), _dev(y)
+    tol = TOL * orc.abs_dot_exact(x, y)
+    if explain:
+        r, cls, qx, qy = q.explain(xd, yd, eps=eps, block=block, split_budget=split, mant_reading=mant)
+        np.testing.assert_array_equal(cls.cpu().numpy(), ref.cls)
+        assert _same_bits(qx.cpu().numpy(), ref.qx)
+        assert _same_bits(qy.cpu().numpy(), ref.qy)
+    else:
+        r = q.qdot(xd, yd, eps=eps, block=block, split_budget=split, mant_reading=mant, path=path)
+    assert r.status == 0
+    assert r.count == tuple(ref.count)
+    assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
+    assert abs(r.value - ref.value) <= tol, (r.value, ref.value, tol)
+    assert r.bound == ref.bound_apriori
+    return r, ref
+
+
+CASES = load_cases()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c.name for c in CASES])
+def test_closed_forms_gpu(q, orc, case):
+    if case.block & (case.block - 1):
+        pytest.skip("the GPU path takes block sizes that are powers of two")
+    xd, yd = _dev(case.x), _dev(case.y)
+    r, cls, qx, qy = q.explain(xd, yd, eps=case.eps, block=case.block, split_budget=case.split,
+                               mant_reading=case.mant)
+    np.testing.assert_array_equal(cls.cpu().numpy(), case.classes)
+    assert r.value == case.z
+    r2 = q.qdot(xd, yd, eps=case.eps, block=case.block, split_budget=case.split, mant_reading=case.mant)
+    assert r2.value == case.z
+
+
+@pytest.mark.parametrize("block", [0, 1, 2, 4, 16, 32, 64, 128, 256, 1024])
+@pytest.mark.parametrize("kind", ["a", "b", "c", "cfg0"])
+def test_parity_grid(q, orc, kind, block):
+    for n in (1, 63, 64, 65, 1000, 4097, 100003):
+        x, y = workloads.pair(kind, n, 17 + n)
+        for eps in (1e-16, 1e-8, 1e-3, 0.5):
+            _check(q, orc, x, y, eps, block)
+            _check(q, orc, x, y, eps, block, explain=False)
+
+
+@pytest.mark.parametrize("block", [0, 1, 32, 256])
+def test_split_and_mant_readings(q, orc, block):
+    x, y = workloads.pair("b", 50000, 3)
+    for split in (0, 1):
+        for mant in (0, 1):
+            for eps in (1e-12, 1e-6, 1e-2):
+                _check(q, orc, x, y, eps, block, split=split, mant=mant)
+
+
+@pytest.mark.parametrize("block", [0, 1, 8, 32, 64, 512])
+def test_misaligned_inputs_use_scalar_loads(q, orc, block):
+    import torch
+    x, y = workloads.pair("b", 30001, 8)
+    xd, yd = _dev(x), _dev(y)
+    # 8-byte aligned views: forces the 64-bit load variant
+    xs, ys = xd[1:], yd[1:]
+    assert xs.data_ptr() % 16 == 8
+    ref = orc.qdot(x[1:], y[1:], eps=1e-6, block=block, explain=True)
+    r, cls, qx, qy = q.explain(xs, ys, eps=1e-6, block=block)
+    np.testing.assert_array_equal(cls.cpu().numpy(), ref.cls)
+    assert _same_bits(qx.cpu().numpy(), ref.qx)
+    assert r.count == tuple(ref.count)
+    assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x[1:], y[1:])
+    r2 = q.qdot(xs, ys, eps=1e-6, block=block)
+    assert r2.count == tuple(ref.count)
+    del torch
+
+
+def test_edge_cases(q, orc):
+    import torch
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    for block in (0, 1, 32, 256):
+        r = q.qdot(e, e, eps=1e-8, block=block)
+        assert r.value == 0.0 and r.n_bins == 0 and sum(r.count) == 0
+        z = torch.zeros(1000, dtype=torch.float64, device="cuda")
+        o = torch.ones(1000, dtype=torch.float64, device="cuda")
+        r = q.qdot(z, o, eps=1e-8, block=block)
+        assert r.value == 0.0 and r.count[4] == 1000 and r.n_bins == 0
+    # a single component, every class reachable (key 3 = e_max, M = 1)
+    for eps, cls in ((2.0**-22, 3), (2.0**-21, 2), (2.0**-8, 1), (4.0, 0)):
+        r, c, _, _ = q.explain(_dev(np.array([3.0])), _dev(np.array([5.0])), eps=eps, block=1)
+        assert int(c.cpu()[0]) == cls
+    # non-finite components are reported, not summed
+    for bad in (np.nan, np.inf, -np.inf):
+        x = np.ones(5000)
+        x[4321] = bad
+        with pytest.raises(q.QdotError):
+            q.qdot(_dev(x), _dev(np.ones(5000)), eps=1e-8, block=32)
+    # subnormal and huge components
+    x = np.array([5e-324, 3 * 2.0**-1074, 1e-310, 1.5, 1e300, -1e308, 2.0**-1022])
+    y = np.array([1e300, 2.0**1000, 3.0, -2.0, 1e-300, 1.0, 7.0])
+    for block in (0, 1, 2, 8):
+        for eps in (1e-16, 1e-3, 10.0):
+            _check(q, orc, x, y, eps, block)
+
+
+def test_invalid_arguments_raise(q):
+    import torch
+    x = torch.ones(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(q.QdotError):
+        q.qdot(x, x, eps=0.0)
+    with pytest.raises(q.QdotError):
+        q.qdot(x, x, eps=1e-8, block=3)
+
+
+def test_dot_fp64_comparator(q, orc):
+    for kind in ("a", "b", "c"):
+        for n in (1, 7, 1000, 1 << 20):
+            x, y = workloads.pair(kind, n, 40 + n)
+            v = q.dot_fp64(_dev(x), _dev(y))
+            assert abs(v - orc.dot_exact(x, y)) <= TOL * orc.abs_dot_exact(x, y)
+
+
+def test_from_host_end_to_end(q, orc):
+    import torch
+    x, y = workloads.pair("b", 200001, 77)
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.from_numpy(y).pin_memory()
+    ref = orc.qdot(x, y, eps=1e-8, block=32)
+    r = q.from_host(xh, yh, eps=1e-8, block=32)
+    assert r.count == tuple(ref.count)
+    assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
+
+
+def test_deterministic_repeat(q, orc):
+    x, y = workloads.pair("c", 1 << 20, 5)
+    xd, yd = _dev(x), _dev(y)
+    vals = {q.qdot(xd, yd, eps=1e-3, block=b).value for b in (32,) for _ in range(5)}
+    assert len(vals) == 1
+
+
+@pytest.mark.parametrize("block", [1, 32, 256])
+def test_full_size_lognormal(q, orc, block):
+    """n = 2^28, lognormal sigma = 4, eps = 1e-8: the benchmark's launch shape,
+    checked against a full oracle run."""
+    n = 1 << 28
+    x, y = workloads.pair("b", n, 2106)
+    xd, yd = _dev(x), _dev(y)
+    r = q.qdot(xd, yd, eps=1e-8, block=block)
+    ref = orc.qdot(x, y, eps=1e-8, block=block)
+    assert r.count == tuple(ref.count)
+    assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
+    assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
