@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of qdot on one GB300 (or N replicas): prints ONE JSON line.
+
+Step = one qdot call over the whole workload (every row of the hot path:
+exponent keys, statistics, selection, quantization, exact accumulation,
+final rounding).  Default workload: n = 2^28 float64 components per vector,
+x and y lognormal (sigma = 4) with random signs, blocks of 32, eps = 1e-8.
+The two input vectors (4 GiB together) are larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs an
+independent replica on its own GPU and data (weak scaling, no collective on
+the data path); rank 0 prints the line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "qdot HBM GB/s and % of roofline vs plain FP64 dot on GB300; CG time-to-1e-10"
+DIST_NAMES = {"a": "uniform[-1,1]", "b": "lognormal(sigma=4) with random sign",
+              "c": "uniform[-1,1] with 1% of entries x1e6", "cfg0": "+-10^U(-8,0)"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1 << 28)
+    ap.add_argument("--dist", default="b", choices=list(DIST_NAMES))
+    ap.add_argument("--block", type=int, default=32)
+    ap.add_argument("--eps", type=float, default=1e-8)
+    ap.add_argument("--path", default="auto", choices=["auto", "two_pass", "one_pass"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    """Barrier and max-over-ranks on the host (gloo); a no-op for one rank."""
+
+    def __init__(self, world):
+        self.world = world
+        if world > 1:
+            import torch.distributed as td
+            td.init_process_group(backend="gloo")
+            self.td = td
+
+    def barrier(self):
+        if self.world > 1:
+            self.td.barrier()
+
+    def max(self, v: float) -> float:
+        if self.world == 1:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64)
+        self.td.all_reduce(t, op=self.td.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self.td.destroy_process_group()
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, enabled: bool):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"qdot_clocks_{os.getpid()}.csv")
+        if enabled:
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
+                                              "--format=csv,noheader,nounits", "-lms", "100"],
+                                             stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            except (OSError, FileNotFoundError):
+                self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2105_00115_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, n: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to n components; None if absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return float(ent["dram_bytes"]) * n / float(ent["n"])
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, on the host cores, each
+    step a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    oracle.build()
+    m = min(args.n, 1 << 22)
+    x, y = workloads.pair(args.dist, m, 2106)
+    for _ in range(args.warmup):
+        oracle.qdot(x, y, eps=args.eps, block=args.block)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.qdot(x, y, eps=args.eps, block=args.block)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    gbs = 16.0 * m * args.steps / total / 1e9
+    sample = f"first 2^{m.bit_length() - 1} components of the {DIST_NAMES[args.dist]} workload per step"
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"single qdot, n=2^{args.n.bit_length() - 1}, {DIST_NAMES[args.dist]}, block={args.block}, "
+                        f"eps={args.eps:g}",
+            "n": args.n, "distribution": DIST_NAMES[args.dist], "block": args.block, "eps": args.eps,
+            "split_budget": 1, "mant_reading": 0, "seed": 2106,
+            "l2": "inputs 4 GiB per step > 129 MB L2 (no flush needed)" if args.n >= (1 << 24)
+                  else "inputs smaller than L2"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2105_00115_gb300 as q
+    import workloads
+    from paper_2105_00115_gb300 import build as qbuild
+
+    qbuild.build()
+    torch.cuda.set_device(local)
+    dist = Dist(world)
+    lib = q.load()
+    n = args.n
+    x, y = workloads.pair(args.dist, n, 2106 + rank)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.from_numpy(y).cuda()
+    stream = torch.cuda.current_stream()
+    p = q.params(args.eps, args.block, 1, 0, args.path)
+    import ctypes
+    ws = torch.empty(max(lib.qdot_workspace_size(n, ctypes.byref(p)), 256), dtype=torch.uint8, device="cuda")
+    out = torch.empty(80, dtype=torch.uint8, device="cuda")
+    launches = int(lib.qdot_kernel_launches(n, ctypes.byref(p), 1))
+
+    def step():
+        q.qdot_async(xd, yd, args.eps, args.block, 1, 0, args.path, out=out, ws=ws, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    res = q.decode_result(out.cpu().numpy())
+
+    # timed region: K steps, per-step kernel events, clocks sampled meanwhile
+    kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for ev in kb + ke:  # materialise the CUDA events the library records into
+        ev.record(stream)
+    clocks = Clocks(local, not args.no_clocks)
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(args.steps):
+        lib.qdot_set_kernel_events(ctypes.c_void_p(kb[k].cuda_event), ctypes.c_void_p(ke[k].cuda_event))
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    lib.qdot_set_kernel_events(None, None)
+    dist.barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = statistics.mean(kb[k].elapsed_time(ke[k]) for k in range(args.steps))
+    total_ms = dist.max(total_ms)
+    kern_ms = dist.max(kern_ms)
+    value = world * args.steps * 16.0 * n / (total_ms * 1e-3) / 1e9
+
+    # comparator: plain FP64 dot on the same data, same protocol
+    dws = torch.empty(lib.qdot_dot_fp64_workspace_size(), dtype=torch.uint8, device="cuda")
+    dout = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def dstep():
+        lib.qdot_dot_fp64(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), n,
+                          ctypes.c_void_p(dout.data_ptr()), ctypes.c_void_p(dws.data_ptr()), dws.numel(),
+                          ctypes.c_void_p(stream.cuda_stream))
+
+    for _ in range(3):
+        dstep()
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(args.steps):
+        dstep()
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dot_ms = dist.max(d0.elapsed_time(d1)) / args.steps
+    dot_gbs = 16.0 * n / (dot_ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.from_numpy(y).pin_memory()
+        q.from_host(xh, yh, args.eps, args.block, 1, 0, args.path, x_dev=xd, y_dev=yd, ws=ws)
+        ksteps = min(args.steps, 5)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        for _ in range(ksteps):
+            q.from_host(xh, yh, args.eps, args.block, 1, 0, args.path, x_dev=xd, y_dev=yd, ws=ws)
+        e_s = dist.max(time.perf_counter() - e0)
+        e2e = {"value": world * ksteps * 16.0 * n / e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": 80, "steps": ksteps}
+
+    # CPU baseline: the oracle on a bounded prefix of the same data (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        m = min(n, 1 << 26)
+        xs, ys = np.ascontiguousarray(x[:m]), np.ascontiguousarray(y[:m])
+        c0 = time.perf_counter()
+        oracle.qdot(xs, ys, eps=args.eps, block=args.block)
+        c_s = time.perf_counter() - c0
+        cpu = {"value": 16.0 * m / c_s / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"first 2^{m.bit_length() - 1} of the 2^{n.bit_length() - 1} components of the same x, y "
+                         f"({c_s:.1f} s, single thread)"}
+
+    peak, peak_src = measured_peak_hbm()
+    kernel = "k_onepass" if lib.qdot_select_path(n, ctypes.byref(p), 1) == 2 else "k_apply"
+    achieved = 16.0 * n / (kern_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_src, "kernel": kernel, "algorithmic_bytes_per_launch": 16 * n,
+                     "traffic": recorded_traffic(kernel, n)},
+        "pct_of_roofline": 100.0 * value / peak,
+        "fp64_dot": {"value": dot_gbs, "unit": "GB/s", "ms": dot_ms, "frac": dot_gbs / peak,
+                     "qdot_over_dot_time": (total_ms / args.steps) / dot_ms},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+        "clocks": clk,
+        "result": {"value": res.value, "count": list(res.count), "n_bins": res.n_bins, "e_max": res.e_max,
+                   "f": res.f, "status": res.status},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

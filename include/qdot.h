@@ -33,7 +33,8 @@
  *             q(v) = v for DOUBLE, 0 for PERF and ZERO.
  *   z         sum_i q(x_i) q(y_i), evaluated with exact integer arithmetic and
  *             rounded once to the nearest double (exact up to a truncation of at
- *             most n 2^(e_max - 97) for n <= 2^28; see qdot()).
+ *             most n 2^(e_max - L), L = min(104, 124 - ceil(log2 n)), plus, on the
+ *             one-pass path, a relative 2^-45 per block; see qdot()).
  *
  * Errors: every entry point returns a qdot_status.  Argument errors are
  * detected on the host before anything is launched (nothing is written).  Data
@@ -93,7 +94,7 @@ typedef struct {
 
 /* The parameter selection of one call (Algorithm 2 output), compact form:
  * the class of every key.  For block == 0 the key is e_i; for block == B it
- * is the block key ceil(log2 M_b) + u_b.  4264 bytes. */
+ * is the block key ceil(log2 M_b) + u_b.  4272 bytes. */
 typedef struct {
   int32_t e_max, e_min, f, status;
   int64_t n_bins;
@@ -155,6 +156,22 @@ qdot_status qdot_dot_fp64(const double* x, const double* y, int64_t n, double* o
 qdot_status qdot_from_host(const double* x_host, const double* y_host, int64_t n, const qdot_params* p,
                            qdot_result* out_host, double* x_dev, double* y_dev, qdot_result* out_dev, void* ws,
                            size_t ws_bytes, void* stream);
+
+/* Number of kernels one qdot() call with these arguments launches (0 on
+ * invalid parameters); `aligned16` tells whether x and y are 16-byte aligned. */
+int32_t qdot_kernel_launches(int64_t n, const qdot_params* p, int32_t aligned16);
+
+/* The path qdot() takes for these arguments: QDOT_PATH_ONE_PASS or
+ * QDOT_PATH_TWO_PASS (0 on invalid parameters). */
+int32_t qdot_select_path(int64_t n, const qdot_params* p, int32_t aligned16);
+
+/* Measurement hook.  When begin and end are both non-NULL (cudaEvent_t
+ * handles created by the caller), every later qdot() on the calling thread
+ * records `begin` on the call's stream right before its main streaming kernel
+ * (the one-pass kernel, or the second pass of the two-pass path) and `end`
+ * right after it, so the caller can time that kernel alone.  Pass NULL, NULL
+ * to stop.  Not part of the method. */
+void qdot_set_kernel_events(void* begin, void* end);
 
 /* Message for the last failing call on the calling thread ("" if none). */
 const char* qdot_last_error(void);

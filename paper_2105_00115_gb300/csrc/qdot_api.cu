@@ -10,8 +10,13 @@
 namespace qd {
 
 static thread_local std::string g_error;
+static thread_local cudaEvent_t g_ev_begin = nullptr, g_ev_end = nullptr;
 void set_error(const std::string& msg) { g_error = msg; }
 void clear_error() { g_error.clear(); }
+void kernel_events(cudaEvent_t* begin, cudaEvent_t* end) {
+  *begin = g_ev_begin;
+  *end = g_ev_end;
+}
 
 const DeviceInfo& device_info() {
   static std::mutex mu;
@@ -227,6 +232,25 @@ qdot_status qdot_from_host(const double* x_host, const double* y_host, int64_t n
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail("qdot_from_host: synchronize", e);
   return QDOT_OK;
+}
+
+int32_t qdot_kernel_launches(int64_t n, const qdot_params* p, int32_t al16) {
+  std::string why;
+  if (!valid_params(n, p, &why)) return 0;
+  PathChoice c = choose_path(n, p, al16 != 0);
+  if (c == kOnePass) return one_pass_launches(n, p);
+  return 4;  // stats, select, apply, final
+}
+
+int32_t qdot_select_path(int64_t n, const qdot_params* p, int32_t al16) {
+  std::string why;
+  if (!valid_params(n, p, &why)) return 0;
+  return choose_path(n, p, al16 != 0) == kOnePass ? QDOT_PATH_ONE_PASS : QDOT_PATH_TWO_PASS;
+}
+
+void qdot_set_kernel_events(void* begin, void* end) {
+  g_ev_begin = (begin && end) ? static_cast<cudaEvent_t>(begin) : nullptr;
+  g_ev_end = (begin && end) ? static_cast<cudaEvent_t>(end) : nullptr;
 }
 
 const char* qdot_last_error(void) { return g_error.c_str(); }

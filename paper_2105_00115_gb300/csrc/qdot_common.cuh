@@ -190,12 +190,13 @@ __device__ __forceinline__ i128 warp_sum_i128(i128 v) {
   return v;
 }
 
-// Largest integer L <= 104 with the fixed-point range of n products below 2^e_max+2
-// fitting a signed 128-bit accumulator: L = min(104, 125 - ceil(log2 n)).
+// Fraction bits L of the fixed-point accumulator (LSB 2^(e_max - L)): every
+// |q(x_i) q(y_i)| <= 2^(e_max + 2), so n of them stay below 2^(L + 2 + ceil(log2 n))
+// <= 2^126 in units of the LSB with L = min(104, 124 - ceil(log2 n)).
 __host__ __device__ inline int fixed_point_bits(long long n) {
   int c = 0;
   while (c < 63 && (1ll << c) < n) ++c;
-  int L = 125 - c;
+  int L = 124 - c;
   return L < 104 ? L : 104;
 }
 

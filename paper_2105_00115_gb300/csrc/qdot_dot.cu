@@ -9,7 +9,7 @@
 namespace qd {
 namespace {
 
-constexpr int kDotThreads = 512;
+constexpr int kDotThreads = 256;
 constexpr int kDotMaxGrid = 4096;
 
 __global__ void __launch_bounds__(kDotThreads) k_dot(const double* __restrict__ x, const double* __restrict__ y,
@@ -66,7 +66,7 @@ size_t dot_fp64_workspace() { return sizeof(double) * kDotMaxGrid; }
 
 cudaError_t launch_dot_fp64(const double* x, const double* y, int64_t n, double* out, void* ws, cudaStream_t st) {
   const DeviceInfo& di = device_info();
-  int grid = (di.sms > 0 ? di.sms : 152) * 4;  // 2048 threads per SM
+  int grid = (di.sms > 0 ? di.sms : 152) * 4;  // 1024 threads per SM, two loads in flight each
   if (grid > kDotMaxGrid) grid = kDotMaxGrid;
   double* part = static_cast<double*>(ws);
   k_dot<<<grid, kDotThreads, 0, st>>>(x, y, n, part);

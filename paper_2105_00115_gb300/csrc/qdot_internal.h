@@ -15,6 +15,9 @@ namespace qd {
 void set_error(const std::string& msg);
 void clear_error();
 
+// Events of qdot_set_kernel_events() for the calling thread (may be null).
+void kernel_events(cudaEvent_t* begin, cudaEvent_t* end);
+
 // Device facts cached per device ordinal.
 struct DeviceInfo {
   int sms = 0;
@@ -62,6 +65,7 @@ struct OnePassPlan {
 };
 bool one_pass_supported(int64_t n, const qdot_params* p, bool aligned16);
 OnePassPlan plan_one_pass(int64_t n, const qdot_params* p);
+int one_pass_launches(int64_t n, const qdot_params* p);
 cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const qdot_params* p,
                             const OnePassPlan& plan, void* ws, qdot_result* out, qdot_selection* sel,
                             cudaStream_t stream);

@@ -116,8 +116,55 @@ __device__ __forceinline__ void segment_reduce(int& u, int& M, int lanes) {
 // ---------------------------------------------------------------------------
 // Pass 1
 // ---------------------------------------------------------------------------
+// Components of a row are "plain" when each of x_i, y_i is a normal double or
+// zero; for plain rows the key is read from the exponent fields directly
+// (e_i + 2046 = biased(x_i) + biased(y_i)), otherwise the general decoder runs.
+__device__ __forceinline__ bool plain_pair(uint64_t a, uint64_t b) {
+  const uint32_t ha = (uint32_t)(a >> 32), hb = (uint32_t)(b >> 32);
+  const bool za = ((ha & 0x7FFFFFFFu) | (uint32_t)a) == 0u, zb = ((hb & 0x7FFFFFFFu) | (uint32_t)b) == 0u;
+  return ((ha & 0x7FF00000u) - 0x00100000u < 0x7FE00000u || za) &&
+         ((hb & 0x7FF00000u) - 0x00100000u < 0x7FE00000u || zb);
+}
+
+template <bool GENERAL>
+__device__ __forceinline__ Decoded decode_fast(uint64_t xb, uint64_t yb, bool valid) {
+  if (GENERAL) return decode(xb, yb, valid);
+  Decoded d;
+  const uint32_t hx = (uint32_t)(xb >> 32), hy = (uint32_t)(yb >> 32);
+  const bool z = (((hx & 0x7FFFFFFFu) | (uint32_t)xb) == 0u) || (((hy & 0x7FFFFFFFu) | (uint32_t)yb) == 0u);
+  d.bad = false;
+  d.nz = valid && !z;
+  d.zero = valid && z;
+  d.key = d.nz ? (int)(((hx & 0x7FF00000u) + (hy & 0x7FF00000u)) >> 20) - 2046 : kNeutralMax;
+  return d;
+}
+
+template <int MODE, int VEC, bool GENERAL>
+__device__ __forceinline__ void stats_row(const Row<VEC>& rw, int lane, int seg_lanes, int& emax, int& emin,
+                                          long long& nb, long long& zeros, int& bad, unsigned int* s_hist) {
+  int u = kNeutralMax, M = 0;
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    Decoded d = decode_fast<GENERAL>(rw.xb[j], rw.yb[j], rw.valid[j]);
+    bad |= d.bad;
+    zeros += d.zero;
+    if (d.nz) {
+      emin = min(emin, d.key);
+      u = max(u, d.key);
+      M += 1;
+      if (MODE == kModeExact) atomicAdd(&s_hist[d.key - kKeyMin], 1u);
+    }
+  }
+  emax = max(emax, u);
+  if (MODE == kModeBlock1) nb += M;
+  if (MODE == kModeBlockSmall) {
+    segment_reduce(u, M, seg_lanes);
+    if ((lane & (seg_lanes - 1)) == 0) nb += (M > 0);
+  }
+}
+
 template <int MODE, int VEC>
-__global__ void __launch_bounds__(kThreads) k_stats(const double* __restrict__ x, const double* __restrict__ y,
+__global__ void __launch_bounds__(kThreads, 4) k_stats(const double* __restrict__ x, const double* __restrict__ y,
                                                     long long n, int log2b, StatsRec* __restrict__ recs,
                                                     unsigned long long* __restrict__ hist,
                                                     int16_t* __restrict__ bkeys) {
@@ -138,28 +185,27 @@ __global__ void __launch_bounds__(kThreads) k_stats(const double* __restrict__ x
   if (MODE != kModeBlockLarge) {
     const long long nrows = (n + R - 1) / R;
     const int seg_lanes = (MODE == kModeBlockSmall) ? ((1 << log2b) / VEC) : 1;
-    for (long long row = gwarp; row < nrows; row += nwarps) {
-      Row<VEC> rw;
-      load_row<VEC, false>(x, y, n, row, lane, rw);
-      int u = kNeutralMax, M = 0;
+    long long row = gwarp;
+    // two rows in flight per warp
+    for (; row + nwarps < nrows; row += 2 * nwarps) {
+      Row<VEC> r0, r1;
+      load_row<VEC, false>(x, y, n, row, lane, r0);
+      load_row<VEC, false>(x, y, n, row + nwarps, lane, r1);
+      bool plain = true;
 #pragma unroll
-      for (int j = 0; j < VEC; ++j) {
-        Decoded d = decode(rw.xb[j], rw.yb[j], rw.valid[j]);
-        bad |= d.bad;
-        zeros += d.zero;
-        if (d.nz) {
-          emax = max(emax, d.key);
-          emin = min(emin, d.key);
-          u = max(u, d.key);
-          M += 1;
-          if (MODE == kModeExact) atomicAdd(&s_hist[d.key - kKeyMin], 1u);
-        }
+      for (int j = 0; j < VEC; ++j) plain &= plain_pair(r0.xb[j], r0.yb[j]) && plain_pair(r1.xb[j], r1.yb[j]);
+      if (__all_sync(0xffffffffu, plain)) {
+        stats_row<MODE, VEC, false>(r0, lane, seg_lanes, emax, emin, nb, zeros, bad, s_hist);
+        stats_row<MODE, VEC, false>(r1, lane, seg_lanes, emax, emin, nb, zeros, bad, s_hist);
+      } else {
+        stats_row<MODE, VEC, true>(r0, lane, seg_lanes, emax, emin, nb, zeros, bad, s_hist);
+        stats_row<MODE, VEC, true>(r1, lane, seg_lanes, emax, emin, nb, zeros, bad, s_hist);
       }
-      if (MODE == kModeBlock1) nb += M;
-      if (MODE == kModeBlockSmall) {
-        segment_reduce(u, M, seg_lanes);
-        if ((lane & (seg_lanes - 1)) == 0) nb += (M > 0);
-      }
+    }
+    for (; row < nrows; row += nwarps) {
+      Row<VEC> r0;
+      load_row<VEC, false>(x, y, n, row, lane, r0);
+      stats_row<MODE, VEC, true>(r0, lane, seg_lanes, emax, emin, nb, zeros, bad, s_hist);
     }
   } else {
     const long long B = 1ll << log2b;
@@ -486,6 +532,206 @@ __global__ void __launch_bounds__(kThreads) k_apply(const double* __restrict__ x
 }
 
 // ---------------------------------------------------------------------------
+// Pass 2, fast form (no per-component output).
+//
+// With the classes known, component i contributes q(x_i) q(y_i).  Both
+// quantized operands are formed as doubles with their significand in [1, 2]:
+// x_i's exponent field is set to 1023 - d (d = e_max - e_i, so the product is
+// scaled by 2^-e_max), y_i's to 1023, and the significand is rounded to the
+// class precision (ties to even) by an integer add-and-mask on the bit pattern
+// (a carry out of the significand moves into the exponent field, as it
+// should).  One fused multiply-add per component accumulates the exact
+// product on the FP64 pipe; every 32 rows the FP64 partial (at most 64 terms,
+// relative error <= 64 * 2^-53) is added exactly into the 128-bit fixed-point
+// accumulator.
+// ---------------------------------------------------------------------------
+struct ClassRound {
+  unsigned long long add;   // 2^(k-1) - 1 for rounding at bit k
+  unsigned long long keep;  // clears the k dropped bits (0 for PERF / ZERO)
+  unsigned long long lsb;   // 2^k (0 when nothing is dropped)
+  unsigned long long inc;   // packed class counter increment
+};
+
+__device__ __forceinline__ i128 double_to_fixed(double v, int L) {
+  // v * 2^L truncated toward zero (|v| < 2^12)
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int be = (int)((b >> 52) & 0x7FFu);
+  if (be == 0) return 0;  // |v| < 2^-1022: below any LSB used here
+  const uint64_t M = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = be - 1075 + L;  // v = M 2^(be - 1075)
+  i128 m = sh >= 0 ? ((i128)M << sh) : (sh <= -64 ? (i128)0 : (i128)(M >> (-sh)));
+  return (b >> 63) ? -m : m;
+}
+
+template <bool GENERAL>
+__device__ __forceinline__ double quantized_operand(uint64_t bits, uint32_t exp_field, const ClassRound& t) {
+  uint64_t P;
+  if (GENERAL) {
+    const uint64_t X = significand_of(bits);  // normalises subnormals
+    P = (bits & 0x8000000000000000ull) | ((uint64_t)exp_field << 52) | (X & 0x000FFFFFFFFFFFFFull);
+  } else {
+    P = (bits & 0x800FFFFFFFFFFFFFull) | ((uint64_t)exp_field << 52);
+  }
+  P = (P + t.add + ((P & t.lsb) ? 1ull : 0ull)) & t.keep;
+  return __longlong_as_double((long long)P);
+}
+
+template <bool GENERAL>
+__device__ __forceinline__ void apply_component(uint64_t xb, uint64_t yb, int key, int cls, int e_max,
+                                                const ClassRound* tab, double& acc, unsigned long long& packed) {
+  const ClassRound t = tab[cls];
+  const int d = min(e_max - key, 1022);
+  const double qx = quantized_operand<GENERAL>(xb, (uint32_t)(1023 - d), t);
+  const double qy = quantized_operand<GENERAL>(yb, 1023u, t);
+  acc = fma(qx, qy, acc);
+  packed += t.inc;
+}
+
+template <int MODE, int VEC, bool GENERAL>
+__device__ __forceinline__ void apply_row(const Row<VEC>& rw, int lane, int seg_lanes, const uint8_t* lut,
+                                          const ClassRound* tab, int e_max, double (&acc)[VEC],
+                                          unsigned long long& packed, int block_cls_in) {
+  Decoded d[VEC];
+  int u = kNeutralMax, M = 0;
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    d[j] = decode_fast<GENERAL>(rw.xb[j], rw.yb[j], rw.valid[j]);
+    u = max(u, d[j].key);
+    M += d[j].nz;
+  }
+  int bcls = block_cls_in;
+  if (MODE == kModeBlockSmall) {
+    segment_reduce(u, M, seg_lanes);
+    bcls = M > 0 ? (int)lut[ceil_log2_u32((uint32_t)M) + u - kKeyMin] : kZero;
+  }
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    int cls;
+    if (MODE == kModeBlockSmall || MODE == kModeBlockLarge)
+      cls = d[j].nz ? bcls : kZero;
+    else
+      cls = d[j].nz ? (int)lut[d[j].key - kKeyMin] : kZero;
+    apply_component<GENERAL>(rw.xb[j], rw.yb[j], d[j].key, cls, e_max, tab, acc[j], packed);
+  }
+}
+
+template <int MODE, int VEC>
+__global__ void __launch_bounds__(kThreads, 4) k_apply_fast(const double* __restrict__ x,
+                                                         const double* __restrict__ y, long long n, int log2b,
+                                                         const qdot_selection* __restrict__ sel,
+                                                         const Header* __restrict__ hdr,
+                                                         const int16_t* __restrict__ bkeys,
+                                                         ApplyRec* __restrict__ recs) {
+  __shared__ uint8_t s_lut[kKeyCount];
+  __shared__ ClassRound s_tab[5];
+  __shared__ i128 s_sum[kWarps];
+  __shared__ unsigned long long s_cnt[kWarps][4];
+  for (int i = threadIdx.x; i < kKeyCount / 4; i += kThreads)
+    reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
+  if (threadIdx.x < 5) {
+    const int c = threadIdx.x;
+    const int k = c == kHalf ? 42 : (c == kSingle ? 29 : 0);
+    ClassRound t;
+    t.add = k ? (1ull << (k - 1)) - 1ull : 0ull;
+    t.keep = (c == kPerf || c == kZero) ? 0ull : ~((1ull << k) - 1ull);
+    t.lsb = k ? (1ull << k) : 0ull;
+    t.inc = c < 4 ? (1ull << (16 * c)) : 0ull;
+    s_tab[c] = t;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * kThreads) >> 5;
+  constexpr int R = 32 * VEC;
+  const int e_max = sel->e_max;
+  const int L = hdr->L;
+  const bool skip = hdr->status != QDOT_OK;
+  i128 acc = 0;
+  double facc[VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) facc[j] = 0.0;
+  unsigned long long packed = 0, cnt[4] = {0, 0, 0, 0};
+  int rows_since = 0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      acc += double_to_fixed(facc[j], L);
+      facc[j] = 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cnt[c] += (packed >> (16 * c)) & 0xFFFFull;
+    packed = 0;
+    rows_since = 0;
+  };
+
+  if (!skip && MODE != kModeBlockLarge) {
+    const long long nrows = (n + R - 1) / R;
+    const int seg_lanes = (MODE == kModeBlockSmall) ? ((1 << log2b) / VEC) : 1;
+    long long row = gwarp;
+    for (; row + nwarps < nrows; row += 2 * nwarps) {
+      Row<VEC> r0, r1;
+      load_row<VEC, true>(x, y, n, row, lane, r0);
+      load_row<VEC, true>(x, y, n, row + nwarps, lane, r1);
+      bool plain = true;
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) plain &= plain_pair(r0.xb[j], r0.yb[j]) && plain_pair(r1.xb[j], r1.yb[j]);
+      if (__all_sync(0xffffffffu, plain)) {
+        apply_row<MODE, VEC, false>(r0, lane, seg_lanes, s_lut, s_tab, e_max, facc, packed, kZero);
+        apply_row<MODE, VEC, false>(r1, lane, seg_lanes, s_lut, s_tab, e_max, facc, packed, kZero);
+      } else {
+        apply_row<MODE, VEC, true>(r0, lane, seg_lanes, s_lut, s_tab, e_max, facc, packed, kZero);
+        apply_row<MODE, VEC, true>(r1, lane, seg_lanes, s_lut, s_tab, e_max, facc, packed, kZero);
+      }
+      if (++rows_since >= 16) flush();
+    }
+    for (; row < nrows; row += nwarps) {
+      Row<VEC> r0;
+      load_row<VEC, true>(x, y, n, row, lane, r0);
+      apply_row<MODE, VEC, true>(r0, lane, seg_lanes, s_lut, s_tab, e_max, facc, packed, kZero);
+    }
+  } else if (!skip) {
+    const long long B = 1ll << log2b;
+    const long long nblk = (n + B - 1) / B;
+    const long long rows_per_block = B / R;
+    for (long long blk = gwarp; blk < nblk; blk += nwarps) {
+      const int16_t kb = bkeys[blk];
+      if (kb == kEmptyBlock) continue;
+      const int bcls = (int)s_lut[(int)kb - kKeyMin];
+      for (long long rr = 0; rr < rows_per_block; ++rr) {
+        const long long row = blk * rows_per_block + rr;
+        if (row * R >= n) break;
+        Row<VEC> rw;
+        load_row<VEC, true>(x, y, n, row, lane, rw);
+        apply_row<MODE, VEC, true>(rw, lane, 1, s_lut, s_tab, e_max, facc, packed, bcls);
+        if (++rows_since >= 32) flush();
+      }
+    }
+  }
+  flush();
+
+  acc = warp_sum_i128(acc);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cnt[k] = warp_sum_u64(cnt[k]);
+  const int w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_sum[w] = acc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s_cnt[w][k] = cnt[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ApplyRec r;
+    r.sum = 0;
+    for (int k = 0; k < 4; ++k) r.cnt[k] = 0;
+    for (int i = 0; i < kWarps; ++i) {
+      r.sum += s_sum[i];
+      for (int k = 0; k < 4; ++k) r.cnt[k] += s_cnt[i][k];
+    }
+    recs[blockIdx.x] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Final (one CTA of 256 threads)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_final(const ApplyRec* __restrict__ recs, int nrecs,
@@ -548,12 +794,15 @@ cudaError_t launch_mode(const double* x, const double* y, int64_t n, const qdot_
   k_stats<MODE, VEC><<<pl.grid_stats, kThreads, 0, st>>>(x, y, n, pl.log2b, srec, hist, bkeys);
   k_select<<<1, 1024, 0, st>>>(srec, pl.grid_stats, hist, MODE, n, *p, sel, hdr);
   const bool explain = cls || qx || qy;
+  cudaEvent_t ev0, ev1;
+  kernel_events(&ev0, &ev1);
+  if (ev0) cudaEventRecord(ev0, st);
   if (explain)
     k_apply<MODE, VEC, true><<<pl.grid_apply, kThreads, 0, st>>>(x, y, n, pl.log2b, sel, hdr, bkeys, arec, cls,
                                                                  qx, qy);
   else
-    k_apply<MODE, VEC, false><<<pl.grid_apply, kThreads, 0, st>>>(x, y, n, pl.log2b, sel, hdr, bkeys, arec,
-                                                                  nullptr, nullptr, nullptr);
+    k_apply_fast<MODE, VEC><<<pl.grid_apply, kThreads, 0, st>>>(x, y, n, pl.log2b, sel, hdr, bkeys, arec);
+  if (ev1) cudaEventRecord(ev1, st);
   k_final<<<1, 256, 0, st>>>(arec, pl.grid_apply, sel, hdr, out);
   return cudaGetLastError();
 }
@@ -590,8 +839,8 @@ TwoPassPlan plan_two_pass(int64_t n, const qdot_params* p, bool aligned16) {
   }
   const DeviceInfo& di = device_info();
   const int sms = di.sms > 0 ? di.sms : 152;
-  pl.grid_stats = sms * 8;   // 2048 threads per SM
-  pl.grid_apply = sms * 8;
+  pl.grid_stats = sms * 4;   // 1024 threads per SM, two rows in flight per warp
+  pl.grid_apply = sms * 4;
   pl.nblocks = (p->block > 0) ? (n + p->block - 1) / p->block : 0;
   size_t off = 0;
   pl.off_sel = off;
