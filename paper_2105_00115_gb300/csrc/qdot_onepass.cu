@@ -120,17 +120,6 @@ __device__ __forceinline__ void load_chunk(const double* __restrict__ x, const d
   }
 }
 
-// Every component of the chunk is present, finite, normal and nonzero.
-__device__ __forceinline__ bool chunk_plain(const Chunk& ch) {
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t ax = (uint32_t)(ch.x[j] >> 32) & 0x7FF00000u, ay = (uint32_t)(ch.y[j] >> 32) & 0x7FF00000u;
-    ok &= ch.valid[j] && (ax - 0x00100000u < 0x7FE00000u) && (ay - 0x00100000u < 0x7FE00000u);
-  }
-  return ok;
-}
-
 __device__ __forceinline__ void rebase(int cmax, int& u_run, long long& aH, long long& aS, double& aD) {
   if (cmax > u_run) {
     if (u_run != kNone) {
@@ -143,19 +132,33 @@ __device__ __forceinline__ void rebase(int cmax, int& u_run, long long& aH, long
   }
 }
 
-template <int LOG2B>
-__device__ __forceinline__ void chunk_fast(const Chunk& ch, int& u_run, long long& aH, long long& aS, double& aD,
-                                           int& kmin) {
-  constexpr int K = LOG2B;
-  int key[8];
-  int cmax = kNone;
+// Keys of a chunk and whether every component is present, finite, normal and
+// nonzero ("plain": the fast path applies).  Keys are biased by 2046.
+__device__ __forceinline__ bool chunk_keys(const Chunk& ch, int (&key)[8], int& cmax, int& kmin) {
+  uint32_t amin = 0xFFFFFFFFu, amax = 0u;
+  bool all_valid = true;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const uint32_t hx = (uint32_t)(ch.x[j] >> 32), hy = (uint32_t)(ch.y[j] >> 32);
-    key[j] = (int)(((hx & 0x7FF00000u) + (hy & 0x7FF00000u)) >> 20);  // e_i + 2046
+    const uint32_t ax = (uint32_t)(ch.x[j] >> 32) & 0x7FF00000u, ay = (uint32_t)(ch.y[j] >> 32) & 0x7FF00000u;
+    amin = min(amin, min(ax, ay));
+    amax = max(amax, max(ax, ay));
+    all_valid &= ch.valid[j];
+    key[j] = (int)((ax + ay) >> 20);
     cmax = max(cmax, key[j]);
-    kmin = min(kmin, key[j]);
   }
+  // exponent fields in [1, 2046] on both sides: no zero, subnormal, Inf or NaN
+  const bool plain = all_valid && amin != 0u && amax != 0x7FF00000u;
+  if (plain) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) kmin = min(kmin, key[j]);
+  }
+  return plain;
+}
+
+template <int LOG2B>
+__device__ __forceinline__ void chunk_fast(const Chunk& ch, const int (&key)[8], int cmax, int& u_run,
+                                           long long& aH, long long& aS, double& aD) {
+  constexpr int K = LOG2B;
   cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, 1));
   cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, 2));
   rebase(cmax, u_run, aH, aS, aD);
@@ -171,7 +174,7 @@ __device__ __forceinline__ void chunk_fast(const Chunk& ch, int& u_run, long lon
     aH += ((long long)(xh * (int)half_sig(my, ly)) << (40 - K)) >> sh;
     const int xs = (int)(single_sig(mx, lx) ^ (uint32_t)sg) - sg;
     aS += (((long long)xs * (long long)single_sig(my, ly)) << (14 - K)) >> sh;
-    const uint32_t ye = (uint32_t)(1023 - min(d, 1022)) << 20;
+    const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
     aD = fma(make_double((hx & 0x800FFFFFu) | 0x3FF00000u, lx), make_double((hy & 0x800FFFFFu) | ye, ly), aD);
   }
 }
@@ -252,8 +255,10 @@ __global__ void __launch_bounds__(kOpThreads, 2) k_onepass(const double* __restr
       ngrp = grp + nwarps;
     }
     if (ngrp < ngroups) load_chunk<LOG2B>(x, y, n, ngrp * kBlocksPerWarp + g, nc, sub, nxt);
-    if (__all_sync(0xffffffffu, chunk_plain(cur))) {
-      chunk_fast<LOG2B>(cur, u_run, aH, aS, aD, kmin);
+    int key[8];
+    int cmax = kNone;
+    if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
+      chunk_fast<LOG2B>(cur, key, cmax, u_run, aH, aS, aD);
       M += 8;
     } else {
       chunk_general<LOG2B>(cur, u_run, aH, aS, aD, M, zeros, kmin, bad);
