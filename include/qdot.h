@@ -157,6 +157,32 @@ qdot_status qdot_from_host(const double* x_host, const double* y_host, int64_t n
                            qdot_result* out_host, double* x_dev, double* y_dev, qdot_result* out_dev, void* ws,
                            size_t ws_bytes, void* stream);
 
+/* Size of the library-owned scratch array used by qdot_static_scratch(). */
+#define QDOT_STATIC_SCRATCH_BYTES (1u << 20)
+
+/* qdot() without a workspace argument, for callers that cannot allocate
+ * device memory: code running under a host application that owns the whole
+ * device allocator (memory reserved up front, a pool with no room left, a
+ * plug-in interface that only passes inputs and outputs) or a deployment that
+ * forbids allocation after start-up.  The paper has no counterpart: this is a
+ * packaging of the same computation.
+ *   x, y, n, p, out, stream  as for qdot(); always the two-pass path.
+ * Scratch: a fixed array of QDOT_STATIC_SCRATCH_BYTES inside the library,
+ * held by every GPU that loads the library until the process exits.  It
+ * fits any n for exact binning and blocks of up to 64 components; larger
+ * blocks need 2 bytes per block on top of a fixed ~90 KB, so n is limited to
+ * about B * 480000.  Arguments that do not fit return QDOT_ERR_WORKSPACE with
+ * a message, before anything is launched.  Nothing is allocated: no
+ * cudaMalloc, cudaFree or allocating library call.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents; each call clears what it needs cleared, but calls
+ * whose executions overlap on the GPU (for example on two streams) race on
+ * the array and must be serialised by the caller. */
+qdot_status qdot_static_scratch(const double* x, const double* y, int64_t n, const qdot_params* p,
+                                qdot_result* out, void* stream);
+
 /* Number of kernels one qdot() call with these arguments launches (0 on
  * invalid parameters); `aligned16` tells whether x and y are 16-byte aligned. */
 int32_t qdot_kernel_launches(int64_t n, const qdot_params* p, int32_t aligned16);

@@ -54,6 +54,7 @@ SIGNATURES = {
     "qdot_dot_fp64_workspace_size": (_SZ, []),
     "qdot_dot_fp64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     "qdot_from_host": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "qdot_static_scratch": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP]),
     "qdot_kernel_launches": (_I32, [_I64, _PP, _I32]),
     "qdot_select_path": (_I32, [_I64, _PP, _I32]),
     "qdot_set_kernel_events": (None, [_VP, _VP]),
