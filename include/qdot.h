@@ -142,6 +142,25 @@ qdot_status qdot(const double* x, const double* y, int64_t n, const qdot_params*
 qdot_status qdot_explain(const double* x, const double* y, int64_t n, const qdot_params* p, qdot_result* out,
                          uint8_t* cls, double* qx, double* qy, void* ws, size_t ws_bytes, void* stream);
 
+/* Batched qdot: `count` independent problems z_j = qdot(x_j, y_j, eps) of
+ * uneven lengths n_j, blocked binning with 32 <= block <= 256, computed in
+ * one persistent streaming launch (plus a planning and a per-problem
+ * finishing kernel).  Each z_j is exactly what qdot() returns for that pair.
+ *   xs, ys   device arrays of `count` device pointers (each 16-byte aligned,
+ *            or the problem's status is QDOT_ERR_ARG).
+ *   ns       device array of `count` lengths (int64, >= 0).
+ *   outs     device array of `count` qdot_result.
+ *   grid_ctas  CTAs of the streaming kernel (0 = two per SM); a tuning knob.
+ *   ws       workspace of qdot_batched_workspace_size(ns_host, count, p)
+ *            bytes, computed from the same lengths on the host; if it is too
+ *            small every problem reports QDOT_ERR_WORKSPACE.
+ * Nothing synchronises with the host, so the call can be recorded in a CUDA
+ * graph and replayed. */
+size_t qdot_batched_workspace_size(const int64_t* ns_host, int32_t count, const qdot_params* p);
+qdot_status qdot_batched(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
+                         const qdot_params* p, qdot_result* outs, int32_t grid_ctas, void* ws, size_t ws_bytes,
+                         void* stream);
+
 /* Plain FP64 dot product x.y (the comparator of the paper's speedup metric,
  * eq. approx-speedup): fused multiply-adds in a fixed order, written to
  * *out (device).  Workspace: qdot_dot_fp64_workspace_size(). */

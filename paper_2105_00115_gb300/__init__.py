@@ -16,7 +16,7 @@ from . import _abi
 from ._abi import Params, QdotError, Result, Selection, check, load
 
 __all__ = ["QdotResult", "QdotError", "qdot", "qdot_async", "explain", "dot_fp64", "from_host", "workspace_size",
-           "load", "params", "decode_result"]
+           "load", "params", "decode_result", "Batch"]
 
 CLASS_NAMES = ("perforate", "half", "single", "double", "zero")
 
@@ -167,3 +167,51 @@ def from_host(x_host, y_host, eps=1e-16, block=32, split_budget=1, mant_reading=
                             ws.numel(), _stream_ptr(stream))
     check(st, lib)
     return QdotResult(res.value, res.bound, res.n_bins, tuple(res.count), res.e_max, res.e_min, res.f, res.status)
+
+
+def _decode_results(buf, count):
+    raw = np.asarray(buf, dtype=np.uint8).reshape(count, ctypes.sizeof(Result))
+    return [decode_result(raw[i]) for i in range(count)]
+
+
+class Batch:
+    """A batch of independent qdot problems on the GPU (one persistent launch).
+
+    ``xs``/``ys`` are lists of 1-D float64 CUDA tensors (16-byte aligned);
+    the pointer and length arrays and the workspace are built once, so
+    ``launch()`` can be recorded in a CUDA graph and replayed."""
+
+    def __init__(self, xs, ys, eps=1e-8, block=32, split_budget=1, mant_reading=0, grid_ctas=0):
+        torch = _torch()
+        lib = load()
+        if len(xs) != len(ys):
+            raise ValueError("xs and ys must have the same number of vectors")
+        for i, (a, b) in enumerate(zip(xs, ys)):
+            _check_vec(a, f"xs[{i}]")
+            _check_vec(b, f"ys[{i}]")
+            if a.numel() != b.numel():
+                raise ValueError(f"pair {i}: lengths differ")
+        self.count = len(xs)
+        self.p = params(eps, block, split_budget, mant_reading, "auto")
+        self.grid_ctas = int(grid_ctas)
+        dev = xs[0].device if xs else torch.device("cuda")
+        self._keep = (xs, ys)
+        self.ns_host = np.array([a.numel() for a in xs], dtype=np.int64)
+        self.xs_dev = torch.tensor([a.data_ptr() for a in xs], dtype=torch.int64, device=dev)
+        self.ys_dev = torch.tensor([b.data_ptr() for b in ys], dtype=torch.int64, device=dev)
+        self.ns_dev = torch.from_numpy(self.ns_host).to(dev)
+        need = lib.qdot_batched_workspace_size(self.ns_host.ctypes.data, self.count, ctypes.byref(self.p))
+        if need == 0 and self.count > 0:
+            raise QdotError(1, "invalid batched qdot parameters (block must be a power of two in [32, 256])")
+        self.ws = _workspace(need, dev)
+        self.outs = torch.empty(max(self.count, 1) * ctypes.sizeof(Result), dtype=torch.uint8, device=dev)
+
+    def launch(self, stream=None):
+        lib = load()
+        st = lib.qdot_batched(_ptr(self.xs_dev), _ptr(self.ys_dev), _ptr(self.ns_dev), self.count,
+                              ctypes.byref(self.p), _ptr(self.outs), self.grid_ctas, _ptr(self.ws), self.ws.numel(),
+                              _stream_ptr(stream))
+        check(st, lib)
+
+    def results(self):
+        return _decode_results(self.outs.cpu().numpy()[: self.count * ctypes.sizeof(Result)], self.count)

@@ -51,6 +51,8 @@ SIGNATURES = {
     "qdot_workspace_size": (_SZ, [_I64, _PP]),
     "qdot": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _SZ, _VP]),
     "qdot_explain": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "qdot_batched_workspace_size": (_SZ, [_VP, _I32, _PP]),
+    "qdot_batched": (ctypes.c_int, [_VP, _VP, _VP, _I32, _PP, _VP, _I32, _VP, _SZ, _VP]),
     "qdot_dot_fp64_workspace_size": (_SZ, []),
     "qdot_dot_fp64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     "qdot_from_host": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),

@@ -1,0 +1,388 @@
+// Batched qdot: many independent pairs (x_j, y_j) of uneven lengths, each a
+// full qdot (Algorithm 3 with blocked binning, 32 <= B <= 256), in one
+// persistent streaming launch.
+//
+//   k_bplan    one CTA: per-pair block and work-group counts, exclusive scans,
+//              argument checks (16-byte alignment, n >= 0), per-pair state.
+//   k_bstream  persistent: the warps split the concatenated work groups (8
+//              blocks each) of all pairs into equal contiguous ranges; every
+//              block's candidate sums go to a record as in the one-pass
+//              kernel; per-pair statistics are merged with one set of atomics
+//              per (warp, pair) run.
+//   k_bfinal   one CTA per pair: f = floor(log2(eps / N_bins)) exactly, the
+//              class of every block record (eq. bin-score-def and eq.
+//              precision-def), exact fixed-point sum, one rounding.
+#include <climits>
+
+#include "qdot_chunk.cuh"
+#include "qdot_common.cuh"
+#include "qdot_internal.h"
+
+namespace qd {
+namespace {
+
+using namespace chunk;
+
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / 32;
+
+struct PairStats {
+  int e_max;                // max block maximum u_b (kNone if none)
+  int e_min;                // min component key
+  int status;               // QDOT_OK, QDOT_ERR_ARG or QDOT_ERR_NONFINITE
+  int pad;
+  unsigned long long nbins; // non-empty blocks
+  unsigned long long zeros; // ZERO components
+};
+
+struct BatchHeader {
+  long long total_groups;
+  long long total_blocks;
+  int status;               // QDOT_OK or QDOT_ERR_WORKSPACE
+  int pad;
+};
+
+__global__ void __launch_bounds__(1024) k_bplan(const double* const* __restrict__ xs,
+                                                const double* const* __restrict__ ys,
+                                                const long long* __restrict__ ns, int count, int log2b,
+                                                long long rec_capacity, long long* __restrict__ gpre,
+                                                long long* __restrict__ bpre, PairStats* __restrict__ ps,
+                                                BatchHeader* __restrict__ hdr) {
+  __shared__ long long s_g[1024], s_b[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int per = (count + T - 1) / T;
+  const int lo = min(count, t * per), hi = min(count, lo + per);
+  long long g = 0, b = 0;
+  for (int p = lo; p < hi; ++p) {
+    const long long n = ns[p];
+    const bool aligned = ((reinterpret_cast<uintptr_t>(xs[p]) | reinterpret_cast<uintptr_t>(ys[p])) & 15u) == 0;
+    const bool ok = n >= 0 && (n == 0 || (aligned && xs[p] && ys[p]));
+    const long long nb = ok ? ((n + (1ll << log2b) - 1) >> log2b) : 0;
+    b += nb;
+    g += (nb + kBlocksPerWarp - 1) / kBlocksPerWarp;
+    PairStats s;
+    s.e_max = kNone;
+    s.e_min = INT_MAX;
+    s.status = ok ? QDOT_OK : QDOT_ERR_ARG;
+    s.pad = 0;
+    s.nbins = 0;
+    s.zeros = 0;
+    ps[p] = s;
+  }
+  s_g[t] = g;
+  s_b[t] = b;
+  __syncthreads();
+  // inclusive scan (Hillis-Steele) of the per-thread sums
+  for (int o = 1; o < T; o <<= 1) {
+    long long vg = t >= o ? s_g[t - o] : 0, vb = t >= o ? s_b[t - o] : 0;
+    __syncthreads();
+    s_g[t] += vg;
+    s_b[t] += vb;
+    __syncthreads();
+  }
+  long long go = t ? s_g[t - 1] : 0, bo = t ? s_b[t - 1] : 0;
+  for (int p = lo; p < hi; ++p) {
+    gpre[p] = go;
+    bpre[p] = bo;
+    const long long n = ns[p];
+    const long long nb = ps[p].status == QDOT_OK ? ((n + (1ll << log2b) - 1) >> log2b) : 0;
+    bo += nb;
+    go += (nb + kBlocksPerWarp - 1) / kBlocksPerWarp;
+  }
+  if (t == T - 1) {
+    gpre[count] = s_g[T - 1];
+    bpre[count] = s_b[T - 1];
+    hdr->total_groups = s_g[T - 1];
+    hdr->total_blocks = s_b[T - 1];
+    hdr->status = s_b[T - 1] > rec_capacity ? QDOT_ERR_WORKSPACE : QDOT_OK;
+    hdr->pad = 0;
+  }
+}
+
+// Largest p with gpre[p] <= gg (pairs with no groups are skipped by the scan).
+__device__ __forceinline__ int find_pair(const long long* __restrict__ gpre, int count, long long gg) {
+  int lo = 0, hi = count;  // gpre[lo] <= gg < gpre[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (gpre[mid] <= gg)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <int LOG2B>
+__global__ void __launch_bounds__(kBThreads, 2) k_bstream(const double* const* __restrict__ xs,
+                                                          const double* const* __restrict__ ys,
+                                                          const long long* __restrict__ ns, int count,
+                                                          const long long* __restrict__ gpre,
+                                                          const long long* __restrict__ bpre,
+                                                          PairStats* __restrict__ ps,
+                                                          const BatchHeader* __restrict__ hdr,
+                                                          BlockRec* __restrict__ recs) {
+  constexpr int kChunks = 1 << (LOG2B - 5);
+  if (hdr->status != QDOT_OK) return;
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, sub = lane & 3;
+  const long long total = hdr->total_groups;
+  const long long gwarp = ((long long)blockIdx.x * kBThreads + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * kBThreads) >> 5;
+  const long long per = (total + nwarps - 1) / nwarps;
+  const long long g0 = min(total, gwarp * per), g1 = min(total, g0 + per);
+  if (g0 >= g1) return;
+
+  // statistics of the current run of groups of one pair
+  int sp = find_pair(gpre, count, g0);
+  long long nbins = 0, zeros_l = 0;
+  int emax_l = kNone, kmin = INT_MAX, bad = 0;
+  auto flush = [&](int p) {
+    const int emax = __reduce_max_sync(0xffffffffu, emax_l);
+    const int km = __reduce_min_sync(0xffffffffu, kmin);
+    const int bd = (int)__reduce_or_sync(0xffffffffu, (unsigned)bad);
+    const unsigned long long nb = warp_sum_u64((unsigned long long)nbins);
+    const unsigned long long zr = warp_sum_u64((unsigned long long)zeros_l);
+    if (lane == 0) {
+      if (emax != kNone) atomicMax(&ps[p].e_max, emax);
+      if (km != INT_MAX) atomicMin(&ps[p].e_min, km - 2046);
+      if (bd) atomicCAS(&ps[p].status, QDOT_OK, QDOT_ERR_NONFINITE);
+      if (nb) atomicAdd(&ps[p].nbins, nb);
+      if (zr) atomicAdd(&ps[p].zeros, zr);
+    }
+    nbins = zeros_l = 0;
+    emax_l = kNone;
+    kmin = INT_MAX;
+    bad = 0;
+  };
+
+  long long gg = g0;
+  int p = sp, c = 0;
+  Chunk cur, nxt;
+  auto load_item = [&](long long item, int pp, int cc, Chunk& ch) {
+    const long long lg = item - gpre[pp];
+    load_chunk<LOG2B>(xs[pp], ys[pp], ns[pp], lg * kBlocksPerWarp + g, cc, sub, ch);
+  };
+  load_item(gg, p, 0, cur);
+  int u_run = kNone, M = 0, zeros = 0;
+  long long aH = 0, aS = 0;
+  double aD = 0.0;
+  while (gg < g1) {
+    // next (group, chunk) of this warp, possibly in the next pair
+    long long ngg = gg;
+    int np = p, nc = c + 1;
+    if (nc == kChunks) {
+      nc = 0;
+      ++ngg;
+      while (np + 1 < count && ngg >= gpre[np + 1]) ++np;
+    }
+    if (ngg < g1) load_item(ngg, np, nc, nxt);
+    int key[8];
+    int cmax = kNone;
+    if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
+      chunk_fast<LOG2B>(cur, key, cmax, u_run, aH, aS, aD);
+      M += 8;
+    } else {
+      chunk_general<LOG2B>(cur, u_run, aH, aS, aD, M, zeros, kmin, bad);
+    }
+    if (c == kChunks - 1) {
+      int kb, u, mb;
+      const long long word = block_record_word<LOG2B>(aH, aS, aD, M, u_run, sub, &kb, &u, &mb);
+      const long long lb = (gg - gpre[p]) * kBlocksPerWarp + g;  // block index within pair p
+      const long long nblk_p = bpre[p + 1] - bpre[p];
+      zeros_l += zeros;
+      if (lb < nblk_p) {
+        if (mb > 0) {
+          nbins += (sub == 0);
+          emax_l = max(emax_l, u);
+        }
+        reinterpret_cast<long long*>(recs + bpre[p] + lb)[sub] = word;
+      }
+      u_run = kNone;
+      M = 0;
+      zeros = 0;
+      aH = aS = 0;
+      aD = 0.0;
+      if (np != p) flush(p);
+    }
+    cur = nxt;
+    gg = ngg;
+    p = np;
+    c = nc;
+  }
+  flush(p < count ? p : count - 1);
+}
+
+__global__ void __launch_bounds__(256) k_bfinal(const long long* __restrict__ ns, const long long* __restrict__ bpre,
+                                                const PairStats* __restrict__ ps, const BatchHeader* __restrict__ hdr,
+                                                const BlockRec* __restrict__ recs, int log2b, qdot_params prm,
+                                                qdot_result* __restrict__ outs) {
+  __shared__ i128 s_sum[8];
+  __shared__ unsigned long long s_cnt[8][4];
+  const int p = blockIdx.x;
+  const PairStats st = ps[p];
+  int status = hdr->status != QDOT_OK ? hdr->status : st.status;
+  const long long nb = (long long)st.nbins;
+  const int e_max = nb > 0 ? st.e_max : 0;
+  const int f = (status == QDOT_OK && nb > 0)
+                    ? floor_log2_ratio(prm.eps, prm.split_budget ? (unsigned long long)nb : 1ull)
+                    : 0;
+  const int mh = prm.mant_reading ? 11 : 10, ms = prm.mant_reading ? 24 : 23;
+  const int L = fixed_point_bits(ns[p] > 0 ? ns[p] : 1);
+  const int lsb = e_max - L;
+  i128 acc = 0;
+  unsigned long long c[4] = {0, 0, 0, 0};
+  if (status == QDOT_OK) {
+    for (long long r = bpre[p] + threadIdx.x; r < bpre[p + 1]; r += blockDim.x) {
+      const longlong2 r0 = reinterpret_cast<const longlong2*>(recs + r)[0];
+      const longlong2 r1 = reinterpret_cast<const longlong2*>(recs + r)[1];
+      const int key = (int)(short)(r1.y & 0xFFFF);
+      if (key == kEmptyKey) continue;
+      const int u = (int)(short)((r1.y >> 16) & 0xFFFF);
+      const unsigned m = (unsigned)((unsigned long long)r1.y >> 32);
+      const int cls = precision_of((long long)key - e_max - f + 1, mh, ms);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c[k] += (cls == k) ? m : 0u;
+      acc += record_candidate(r0.x, r0.y, r1.x, u, cls, log2b, lsb);
+    }
+  }
+  acc = warp_sum_i128(acc);
+  for (int k = 0; k < 4; ++k) c[k] = warp_sum_u64(c[k]);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_sum[w] = acc;
+    for (int k = 0; k < 4; ++k) s_cnt[w][k] = c[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      acc += s_sum[i];
+      for (int k = 0; k < 4; ++k) c[k] += s_cnt[i][k];
+    }
+    qdot_result r;
+    r.status = status;
+    r.n_bins = nb;
+    r.e_max = e_max;
+    r.e_min = nb > 0 ? st.e_min : 0;
+    r.f = f;
+    for (int k = 0; k < 4; ++k) r.count[k] = (int64_t)c[k];
+    r.count[4] = (int64_t)st.zeros;
+    if (status != QDOT_OK) {
+      r.value = __longlong_as_double(0x7FF8000000000000ll);
+      r.bound = r.value;
+    } else {
+      r.value = fixed_to_double(acc, lsb);
+      r.bound = nb > 0 ? fixed_to_double((i128)nb, e_max + f) : 0.0;
+    }
+    outs[p] = r;
+  }
+}
+
+struct BatchLayout {
+  size_t off_hdr, off_gpre, off_bpre, off_ps, off_rec, fixed;
+};
+
+BatchLayout batch_layout(int count) {
+  BatchLayout l;
+  size_t off = 0;
+  l.off_hdr = off;
+  off = align_up(off + sizeof(BatchHeader), 256);
+  l.off_gpre = off;
+  off = align_up(off + sizeof(long long) * (size_t)(count + 1), 256);
+  l.off_bpre = off;
+  off = align_up(off + sizeof(long long) * (size_t)(count + 1), 256);
+  l.off_ps = off;
+  off = align_up(off + sizeof(PairStats) * (size_t)(count > 0 ? count : 1), 256);
+  l.off_rec = off;
+  l.fixed = off;
+  return l;
+}
+
+template <int LOG2B>
+cudaError_t launch_batched_lb(const double* const* xs, const double* const* ys, const long long* ns, int count,
+                              const qdot_params* p, qdot_result* outs, int grid, char* ws, size_t ws_bytes,
+                              cudaStream_t st) {
+  const BatchLayout l = batch_layout(count);
+  auto* hdr = reinterpret_cast<BatchHeader*>(ws + l.off_hdr);
+  auto* gpre = reinterpret_cast<long long*>(ws + l.off_gpre);
+  auto* bpre = reinterpret_cast<long long*>(ws + l.off_bpre);
+  auto* ps = reinterpret_cast<PairStats*>(ws + l.off_ps);
+  auto* recs = reinterpret_cast<BlockRec*>(ws + l.off_rec);
+  const long long capacity = (long long)((ws_bytes - l.fixed) / sizeof(BlockRec));
+  k_bplan<<<1, 1024, 0, st>>>(xs, ys, ns, count, LOG2B, capacity, gpre, bpre, ps, hdr);
+  cudaEvent_t ev0, ev1;
+  kernel_events(&ev0, &ev1);
+  if (ev0) cudaEventRecord(ev0, st);
+  k_bstream<LOG2B><<<grid, kBThreads, 0, st>>>(xs, ys, ns, count, gpre, bpre, ps, hdr, recs);
+  if (ev1) cudaEventRecord(ev1, st);
+  k_bfinal<<<count, 256, 0, st>>>(ns, bpre, ps, hdr, recs, LOG2B, *p, outs);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace qd
+
+using namespace qd;
+
+extern "C" {
+
+size_t qdot_batched_workspace_size(const int64_t* ns_host, int32_t count, const qdot_params* p) {
+  std::string why;
+  if (count < 0 || !p || !valid_params(0, p, &why) || p->block < 32 || p->block > 256) return 0;
+  if (count > 0 && !ns_host) return 0;
+  long long blocks = 0;
+  for (int i = 0; i < count; ++i) {
+    if (ns_host[i] < 0) return 0;
+    blocks += (ns_host[i] + p->block - 1) / p->block;
+  }
+  return batch_layout(count).fixed + align_up(sizeof(chunk::BlockRec) * (size_t)blocks, 256);
+}
+
+qdot_status qdot_batched(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
+                         const qdot_params* p, qdot_result* outs, int32_t grid_ctas, void* ws, size_t ws_bytes,
+                         void* stream) {
+  clear_error();
+  std::string why;
+  if (!p || !valid_params(0, p, &why)) {
+    set_error("qdot_batched: " + (p ? why : std::string("params pointer is NULL")));
+    return QDOT_ERR_ARG;
+  }
+  if (p->block < 32 || p->block > 256) {
+    set_error("qdot_batched: block must be a power of two in [32, 256]");
+    return QDOT_ERR_ARG;
+  }
+  if (count < 0 || (count > 0 && (!xs || !ys || !ns || !outs))) {
+    set_error("qdot_batched: count must be >= 0 and xs, ys, ns, outs non-NULL device arrays");
+    return QDOT_ERR_ARG;
+  }
+  if (grid_ctas < 0) {
+    set_error("qdot_batched: grid_ctas must be >= 0 (0 = default)");
+    return QDOT_ERR_ARG;
+  }
+  if (count == 0) return QDOT_OK;
+  const BatchLayout l = batch_layout(count);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < l.fixed) {
+    set_error("qdot_batched: workspace missing, misaligned or smaller than qdot_batched_workspace_size()");
+    return QDOT_ERR_WORKSPACE;
+  }
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const int grid = grid_ctas > 0 ? grid_ctas : 2 * sms;
+  int lb = 0;
+  while ((1 << lb) < p->block) ++lb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const long long* nsl = reinterpret_cast<const long long*>(ns);
+  cudaError_t e;
+  switch (lb) {
+    case 5: e = launch_batched_lb<5>(xs, ys, nsl, count, p, outs, grid, w, ws_bytes, st); break;
+    case 6: e = launch_batched_lb<6>(xs, ys, nsl, count, p, outs, grid, w, ws_bytes, st); break;
+    case 7: e = launch_batched_lb<7>(xs, ys, nsl, count, p, outs, grid, w, ws_bytes, st); break;
+    default: e = launch_batched_lb<8>(xs, ys, nsl, count, p, outs, grid, w, ws_bytes, st); break;
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("qdot_batched launch: ") + cudaGetErrorString(e));
+    return QDOT_ERR_CUDA;
+  }
+  return QDOT_OK;
+}
+
+}  // extern "C"
