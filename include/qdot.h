@@ -70,7 +70,10 @@ enum { QDOT_PERF = 0, QDOT_HALF = 1, QDOT_SINGLE = 2, QDOT_DOUBLE = 3, QDOT_ZERO
 #define QDOT_KEY_COUNT 4224
 
 /* Execution path for qdot(): chosen automatically unless forced. */
-enum { QDOT_PATH_AUTO = 0, QDOT_PATH_TWO_PASS = 1, QDOT_PATH_ONE_PASS = 2 };
+enum { QDOT_PATH_AUTO = 0, QDOT_PATH_TWO_PASS = 1, QDOT_PATH_ONE_PASS = 2,
+       /* qdot_cg / qdot_power only: every dot product a plain FP64 dot (the
+        * comparator); eps, block, split_budget and mant_reading are ignored */
+       QDOT_PATH_FP64_DOT = 3 };
 
 typedef struct {
   double eps;           /* qdot tolerance eps > 0, finite (Algorithm 3 input) */
@@ -112,6 +115,23 @@ typedef struct {
   const int32_t* col;     /* [nnz] */
   const double* val;      /* [nnz] */
 } qdot_csr;
+
+/* Device-side summary of a qdot_cg() run (64 bytes). */
+typedef struct {
+  int32_t iters;        /* CG iterations taken (k at exit) */
+  int32_t status;       /* QDOT_OK, QDOT_ERR_NOCONV or QDOT_ERR_NONFINITE */
+  double relres;        /* sqrt(c_k) / ||b||, the residual the algorithm holds */
+  double true_relres;   /* ||b - A x|| / ||b|| recomputed at exit (exact dot) */
+  int64_t counts[5];    /* components per class over every qdot of the run */
+} qdot_cg_info;
+
+/* Device-side summary of a qdot_power() run (56 bytes). */
+typedef struct {
+  int32_t iters;        /* iterations taken */
+  int32_t status;       /* QDOT_OK or QDOT_ERR_NONFINITE */
+  double lambda;        /* last eigenvalue estimate */
+  int64_t counts[5];    /* components per class over every qdot of the run */
+} qdot_power_info;
 
 /* ------------------------------------------------------------------------ */
 
@@ -160,6 +180,32 @@ size_t qdot_batched_workspace_size(const int64_t* ns_host, int32_t count, const 
 qdot_status qdot_batched(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
                          const qdot_params* p, qdot_result* outs, int32_t grid_ctas, void* ws, size_t ws_bytes,
                          void* stream);
+
+/* ACG, Algorithm 4 of the paper: conjugate gradients for an SPD matrix A with
+ * both dot products per iteration (p.q and r.r) computed by qdot with
+ * parameters p.  x holds x0 on entry and the iterate on exit.  The loop runs
+ * while k < max_it and sqrt(c_k) / ||b|| > rel_tol, c_k = qdot(r_k, r_k)
+ * (the residual norm the algorithm holds; ||b|| is computed exactly).
+ * info (device) receives the summary; class_hist (device, optional) receives
+ * per iteration k the class counts of qdot(p, q) at [10k, 10k + 5) and of
+ * qdot(r, r) at [10k + 5, 10k + 10) (max_it * 10 int64).  The call
+ * synchronises the stream once per 16 iterations to test convergence.
+ * Workspace: qdot_cg_workspace_size(A->n, p). */
+size_t qdot_cg_workspace_size(int64_t n, const qdot_params* p);
+qdot_status qdot_cg(const qdot_csr* A, const double* b, double* x, double rel_tol, int32_t max_it,
+                    const qdot_params* p, qdot_cg_info* info, int64_t* class_hist, void* ws, size_t ws_bytes,
+                    void* stream);
+
+/* APM, Algorithm 5 of the paper, with the eigenvalue estimate read as the
+ * Rayleigh quotient: for k = 0, 1, ...: w = A x_k; lambda_k = qdot(x_k, w);
+ * c = qdot(w, w); x_{k+1} = w * (1 / sqrt(c)); stop after `iters` iterations
+ * or, when tau > 0, once |lambda_k - lambda_{k-1}| <= tau.  x holds a unit
+ * start vector on entry and the last iterate on exit.  class_hist as for
+ * qdot_cg (x.w counts, then w.w counts).  Workspace:
+ * qdot_power_workspace_size(A->n, p). */
+size_t qdot_power_workspace_size(int64_t n, const qdot_params* p);
+qdot_status qdot_power(const qdot_csr* A, double* x, int32_t iters, double tau, const qdot_params* p,
+                       qdot_power_info* info, int64_t* class_hist, void* ws, size_t ws_bytes, void* stream);
 
 /* Plain FP64 dot product x.y (the comparator of the paper's speedup metric,
  * eq. approx-speedup): fused multiply-adds in a fixed order, written to

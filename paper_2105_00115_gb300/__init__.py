@@ -16,7 +16,7 @@ from . import _abi
 from ._abi import Params, QdotError, Result, Selection, check, load
 
 __all__ = ["QdotResult", "QdotError", "qdot", "qdot_async", "explain", "dot_fp64", "from_host", "workspace_size",
-           "load", "params", "decode_result", "Batch"]
+           "load", "params", "decode_result", "Batch", "Csr", "cg", "power"]
 
 CLASS_NAMES = ("perforate", "half", "single", "double", "zero")
 
@@ -36,6 +36,10 @@ class QdotResult:
     e_min: int
     f: int
     status: int
+
+
+# qdot_status values (include/qdot.h)
+QDOT_OK, QDOT_ERR_ARG, QDOT_ERR_NONFINITE, QDOT_ERR_CUDA, QDOT_ERR_TIMEOUT, QDOT_ERR_WORKSPACE, QDOT_ERR_NOCONV = range(7)
 
 
 def params(eps=1e-16, block=32, split_budget=1, mant_reading=0, path="auto") -> Params:
@@ -215,3 +219,65 @@ class Batch:
 
     def results(self):
         return _decode_results(self.outs.cpu().numpy()[: self.count * ctypes.sizeof(Result)], self.count)
+
+
+class Csr:
+    """A CSR matrix in device memory (int64 row pointers, int32 columns, float64 values)."""
+
+    def __init__(self, rowptr, col, val, device="cuda"):
+        torch = _torch()
+        self.rowptr = torch.as_tensor(np.asarray(rowptr, dtype=np.int64)).to(device)
+        self.col = torch.as_tensor(np.asarray(col, dtype=np.int32)).to(device)
+        self.val = torch.as_tensor(np.asarray(val, dtype=np.float64)).to(device)
+        self.n = self.rowptr.numel() - 1
+        self.abi = _abi.Csr(self.n, self.col.numel(), self.rowptr.data_ptr(), self.col.data_ptr(),
+                            self.val.data_ptr())
+
+
+def _solver_path(dot):
+    if dot not in ("qdot", "fp64"):
+        raise ValueError("dot must be 'qdot' or 'fp64'")
+    return "auto" if dot == "qdot" else "fp64_dot"
+
+
+def cg(A: Csr, b, x0=None, rel_tol=1e-10, max_it=50000, eps=1e-16, block=0, split_budget=1, mant_reading=0,
+       history=False, dot="qdot", stream=None):
+    """ACG (Algorithm 4) on the GPU.  Returns (x, info dict, history or None).
+
+    dot="fp64" runs the same solver with plain FP64 dot products (the comparator)."""
+    torch = _torch()
+    lib = load()
+    _check_vec(b, "b")
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    p = params(eps, block, split_budget, mant_reading, _solver_path(dot))
+    ws = _workspace(lib.qdot_cg_workspace_size(A.n, ctypes.byref(p)), b.device)
+    info = torch.empty(64, dtype=torch.uint8, device=b.device)
+    hist = torch.zeros(max(max_it, 1) * 10, dtype=torch.int64, device=b.device) if history else None
+    check(lib.qdot_cg(ctypes.byref(A.abi), _ptr(b), _ptr(x), float(rel_tol), int(max_it), ctypes.byref(p),
+                      _ptr(info), _ptr(hist), _ptr(ws), ws.numel(), _stream_ptr(stream)), lib)
+    raw = _abi.CgInfo.from_buffer_copy(bytes(info.cpu().numpy()))
+    out = {"iters": raw.iters, "status": raw.status, "relres": raw.relres, "true_relres": raw.true_relres,
+           "counts": tuple(raw.counts)}
+    h = hist[: raw.iters * 10].view(raw.iters, 2, 5).cpu().numpy() if history else None
+    return x, out, h
+
+
+def power(A: Csr, x0, iters=500, tau=0.0, eps=1e-16, block=0, split_budget=1, mant_reading=0, history=False,
+          dot="qdot", stream=None):
+    """APM (Algorithm 5) on the GPU.  Returns (lambda, x, info dict, history or None).
+
+    dot="fp64" runs the same iteration with plain FP64 dot products."""
+    torch = _torch()
+    lib = load()
+    _check_vec(x0, "x0")
+    x = x0.clone()
+    p = params(eps, block, split_budget, mant_reading, _solver_path(dot))
+    ws = _workspace(lib.qdot_power_workspace_size(A.n, ctypes.byref(p)), x.device)
+    info = torch.empty(56, dtype=torch.uint8, device=x.device)
+    hist = torch.zeros(max(iters, 1) * 10, dtype=torch.int64, device=x.device) if history else None
+    check(lib.qdot_power(ctypes.byref(A.abi), _ptr(x), int(iters), float(tau), ctypes.byref(p), _ptr(info),
+                         _ptr(hist), _ptr(ws), ws.numel(), _stream_ptr(stream)), lib)
+    raw = _abi.PowerInfo.from_buffer_copy(bytes(info.cpu().numpy()))
+    out = {"iters": raw.iters, "status": raw.status, "lambda": raw.lambda_, "counts": tuple(raw.counts)}
+    h = hist[: raw.iters * 10].view(raw.iters, 2, 5).cpu().numpy() if history else None
+    return raw.lambda_, x, out, h

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(_PKG, "libqdot.so")
 
 KEY_MIN = -2148
 KEY_COUNT = 4224
-PATHS = {"auto": 0, "two_pass": 1, "one_pass": 2}
+PATHS = {"auto": 0, "two_pass": 1, "one_pass": 2, "fp64_dot": 3}
 STATUS = {0: "QDOT_OK", 1: "QDOT_ERR_ARG", 2: "QDOT_ERR_NONFINITE", 3: "QDOT_ERR_CUDA", 4: "QDOT_ERR_TIMEOUT",
           5: "QDOT_ERR_WORKSPACE", 6: "QDOT_ERR_NOCONV"}
 
@@ -37,7 +37,19 @@ class Csr(ctypes.Structure):
                 ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
+class CgInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("true_relres", ctypes.c_double), ("counts", ctypes.c_int64 * 5)]
+
+
+class PowerInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("lambda_", ctypes.c_double),
+                ("counts", ctypes.c_int64 * 5)]
+
+
 assert ctypes.sizeof(Result) == 80
+assert ctypes.sizeof(CgInfo) == 64
+assert ctypes.sizeof(PowerInfo) == 56
 assert ctypes.sizeof(Params) == 24
 
 # (name, restype, argtypes) for every entry point of include/qdot.h
@@ -53,6 +65,10 @@ SIGNATURES = {
     "qdot_explain": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "qdot_batched_workspace_size": (_SZ, [_VP, _I32, _PP]),
     "qdot_batched": (ctypes.c_int, [_VP, _VP, _VP, _I32, _PP, _VP, _I32, _VP, _SZ, _VP]),
+    "qdot_cg_workspace_size": (_SZ, [_I64, _PP]),
+    "qdot_cg": (ctypes.c_int, [_VP, _VP, _VP, _D, _I32, _PP, _VP, _VP, _VP, _SZ, _VP]),
+    "qdot_power_workspace_size": (_SZ, [_I64, _PP]),
+    "qdot_power": (ctypes.c_int, [_VP, _VP, _I32, _D, _PP, _VP, _VP, _VP, _SZ, _VP]),
     "qdot_dot_fp64_workspace_size": (_SZ, []),
     "qdot_dot_fp64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     "qdot_from_host": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),

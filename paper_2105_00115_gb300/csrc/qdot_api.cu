@@ -134,6 +134,19 @@ qdot_status cuda_fail(const char* what, cudaError_t e) {
 
 }  // namespace
 
+namespace qd {
+size_t qdot_ws_bytes(int64_t n, const qdot_params* p) {
+  return std::max(workspace_for(n, p, true, nullptr), workspace_for(n, p, false, nullptr));
+}
+cudaError_t launch_qdot_auto(const double* x, const double* y, int64_t n, const qdot_params* p, void* ws,
+                             qdot_result* out, cudaStream_t st) {
+  const bool al16 = aligned16(x, y);
+  PathChoice c = choose_path(n, p, al16);
+  if (c == kOnePass) return launch_one_pass(x, y, n, p, plan_one_pass(n, p), ws, out, nullptr, st);
+  return launch_two_pass(x, y, n, p, plan_two_pass(n, p, al16), ws, out, nullptr, nullptr, nullptr, nullptr, st);
+}
+}  // namespace qd
+
 extern "C" {
 
 size_t qdot_workspace_size(int64_t n, const qdot_params* p) {

@@ -70,6 +70,12 @@ cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const q
                             const OnePassPlan& plan, void* ws, qdot_result* out, qdot_selection* sel,
                             cudaStream_t stream);
 
+// qdot() on device buffers with the path qdot() would choose (no checks);
+// ws must hold qdot_workspace_size(n, p) bytes.
+size_t qdot_ws_bytes(int64_t n, const qdot_params* p);
+cudaError_t launch_qdot_auto(const double* x, const double* y, int64_t n, const qdot_params* p, void* ws,
+                             qdot_result* out, cudaStream_t stream);
+
 // Plain FP64 dot.
 cudaError_t launch_dot_fp64(const double* x, const double* y, int64_t n, double* out, void* ws,
                             cudaStream_t stream);

@@ -1,0 +1,134 @@
+"""GPU ACG (Algorithm 4) and APM (Algorithm 5) against the oracle's.
+
+The GPU qdot meets the oracle's value within 1e-13 * sum |x_i y_i| (not bit
+for bit), so iterates drift apart by rounding-sized amounts.  The bar:
+  * first iteration: the class counts of qdot(p0, A p0) equal the oracle's
+    (identical inputs), values within the qdot tolerance;
+  * well-conditioned operator: identical iteration counts, solutions within
+    1e-8 relative;
+  * variable-coefficient (ill-conditioned) operator: both converge, iteration
+    counts within 3%, the true residual small;
+  * power method: eigenvalue within 1e-10 relative of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_00115_gb300 import build as qbuild
+    qbuild.build()
+    import paper_2105_00115_gb300 as qq
+    qq.load()
+    return qq
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("block,eps", [(0, 1e-16), (1, 1e-3), (32, 1e-8), (256, 1e-2)])
+def test_cg_first_iteration(q, orc, block, eps):
+    rp, col, val = workloads.poisson3d(12, 10, 9)
+    n = rp.shape[0] - 1
+    b = workloads.rhs(n)
+    x, info, hist = q.cg(q.Csr(rp, col, val), _dev(b), rel_tol=1e-10, max_it=1, eps=eps, block=block, history=True)
+    xo, it, rr, counts, st = orc.cg(rp, col, val, b, rel_tol=1e-10, max_it=1, eps=eps, block=block)
+    assert info["iters"] == it == 1 and info["status"] == q.QDOT_ERR_NOCONV
+    # p0 = b and q0 = A b are bit-identical on both sides
+    Ab = orc.spmv(rp, col, val, b)
+    ref = orc.qdot(b, Ab, eps=eps, block=block)
+    np.testing.assert_array_equal(hist[0, 0], ref.count)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-12 * np.linalg.norm(xo)
+    assert abs(info["relres"] - rr) <= 1e-10 * rr
+
+
+@pytest.mark.parametrize("block,eps", [(0, 1e-16), (1, 1e-6), (32, 1e-8), (256, 1e-4)])
+def test_cg_well_conditioned(q, orc, block, eps):
+    rp, col, val = workloads.laplace3d(14, 12, 10)
+    n = rp.shape[0] - 1
+    b = workloads.rhs(n)
+    x, info, hist = q.cg(q.Csr(rp, col, val), _dev(b), rel_tol=1e-10, max_it=5000, eps=eps, block=block,
+                        history=True)
+    xo, it, rr, counts, st = orc.cg(rp, col, val, b, rel_tol=1e-10, max_it=5000, eps=eps, block=block)
+    assert st == 0 and info["status"] == 0
+    assert info["iters"] == it
+    assert info["relres"] <= 1e-10 and rr <= 1e-10
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    assert hist.shape == (it, 2, 5) and int(hist.sum()) == sum(info["counts"]) - n  # minus the initial r.r
+    assert info["true_relres"] <= 1e-9
+
+
+@pytest.mark.parametrize("block,eps", [(0, 1e-16), (32, 1e-8)])
+def test_cg_variable_coefficients(q, orc, block, eps):
+    rp, col, val = workloads.poisson3d(12, 10, 9)
+    n = rp.shape[0] - 1
+    b = workloads.rhs(n)
+    A = q.Csr(rp, col, val)
+    x, info, _ = q.cg(A, _dev(b), rel_tol=1e-10, max_it=40000, eps=eps, block=block)
+    xo, it, rr, counts, st = orc.cg(rp, col, val, b, rel_tol=1e-10, max_it=40000, eps=eps, block=block)
+    assert st == 0 and info["status"] == 0 and info["relres"] <= 1e-10
+    assert abs(info["iters"] - it) <= 0.03 * it, (info["iters"], it)
+    # the comparator: the same GPU solver with plain FP64 dot products
+    x64, i64, _ = q.cg(A, _dev(b), rel_tol=1e-10, max_it=40000, dot="fp64")
+    assert i64["status"] == 0 and sum(i64["counts"]) == 0
+    assert abs(info["iters"] - i64["iters"]) <= 0.03 * i64["iters"], (info["iters"], i64["iters"])
+
+
+def test_cg_iteration_cap_and_fp64_mode(q, orc):
+    rp, col, val = workloads.laplace3d(10, 10, 10)
+    n = rp.shape[0] - 1
+    b = workloads.rhs(n)
+    A = q.Csr(rp, col, val)
+    x, info, _ = q.cg(A, _dev(b), rel_tol=1e-14, max_it=7, eps=1e-16, block=0)
+    assert info["iters"] == 7 and info["status"] == q.QDOT_ERR_NOCONV
+    # plain-FP64 mode against a textbook CG in numpy (same recurrences, numpy dots)
+    x64, i64, _ = q.cg(A, _dev(b), rel_tol=1e-10, max_it=5000, dot="fp64")
+    import scipy.sparse as sp
+    M = sp.csr_matrix((val, col, rp), shape=(n, n))
+    xr = np.zeros(n); r = b.copy(); p = r.copy(); c = r @ r; k = 0
+    while k < 5000 and np.sqrt(c) / np.linalg.norm(b) > 1e-10:
+        qv = M @ p; a = c / (p @ qv); xr += a * p; r -= a * qv; cn = r @ r; p = r + (cn / c) * p; c = cn; k += 1
+    assert i64["status"] == 0 and abs(i64["iters"] - k) <= 1
+    assert np.linalg.norm(x64.cpu().numpy() - xr) <= 1e-8 * np.linalg.norm(xr)
+
+
+@pytest.mark.parametrize("block,eps,tau", [(0, 1e-16, 0.0), (0, 1e-7, 0.0), (32, 1e-4, 0.0), (1, 1e-2, 0.0),
+                                           (32, 1e-8, 1e-9)])
+def test_power_matches_oracle(q, orc, block, eps, tau):
+    rp, col, val = workloads.poisson2d(40, 33)
+    n = rp.shape[0] - 1
+    x0 = workloads.unit_start(n)
+    lam, x, info, hist = q.power(q.Csr(rp, col, val), _dev(x0), iters=300, tau=tau, eps=eps, block=block,
+                                 history=True)
+    lo, xo, it, counts, st = orc.power(rp, col, val, x0, iters=300, tau=tau, eps=eps, block=block)
+    assert st == 0 and info["status"] == 0
+    if tau == 0.0:
+        assert info["iters"] == it == 300
+    else:
+        assert abs(info["iters"] - it) <= 1
+    assert abs(lam - lo) <= 1e-10 * abs(lo)
+    assert hist.shape == (info["iters"], 2, 5)
+    assert (hist.sum(axis=2) == n).all()
+    # the first iteration's Rayleigh quotient sees identical inputs
+    ref = orc.qdot(x0, orc.spmv(rp, col, val, x0), eps=eps, block=block)
+    np.testing.assert_array_equal(hist[0, 0], ref.count)
+
+
+def test_power_iters_zero(q):
+    rp, col, val = workloads.poisson2d(8, 8)
+    n = rp.shape[0] - 1
+    x0 = workloads.unit_start(n)
+    lam, x, info, _ = q.power(q.Csr(rp, col, val), _dev(x0), iters=0)
+    assert info["iters"] == 0 and lam == 0.0
+    np.testing.assert_array_equal(x.cpu().numpy(), x0)

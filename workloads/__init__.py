@@ -148,6 +148,11 @@ def poisson3d(nx: int, ny: int, nz: int, seed: int = 2108):
     return _assemble(coefficients(nx * ny * nz, seed), (nx, ny, nz))
 
 
+def laplace3d(nx: int, ny: int, nz: int):
+    """Constant-coefficient 7-point operator (every cell coefficient 1)."""
+    return _assemble(np.ones(nx * ny * nz), (nx, ny, nz))
+
+
 def poisson2d(nx: int, ny: int, seed: int = 2109):
     """5-point SPD operator on an nx x ny grid."""
     return _assemble(coefficients(nx * ny, seed), (nx, ny))
