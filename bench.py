@@ -48,7 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "cg", "power", "backward"])
+    ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-1e-10 summary of the single line")
+    ap.add_argument("--grid", type=int, default=128, help="CG grid edge (cg workload)")
+    ap.add_argument("--eps-sweep", action="store_true", help="cg workload: ACG at eps = 1e-16 .. 1e3")
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--grid-ctas", type=int, default=0)
     return ap.parse_args()
@@ -298,6 +301,192 @@ def run_batched(args, rank, world, local, dist, lib):
     }
 
 
+def cg_problem(edge: int):
+    import torch
+
+    import paper_2105_00115_gb300 as q
+    import workloads
+    rp, col, val = workloads.poisson3d(edge, edge, edge)
+    b = workloads.rhs(rp.shape[0] - 1)
+    return q.Csr(rp, col, val), torch.from_numpy(b).cuda(), int(col.shape[0])
+
+
+def timed_cg(A, bd, eps, block, dot, reps=1, max_it=200000):
+    """(seconds per solve, info) of qdot_cg to relative residual 1e-10 from x0 = 0."""
+    import torch
+
+    import paper_2105_00115_gb300 as q
+    times = []
+    info = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, info, _ = q.cg(A, bd, rel_tol=1e-10, max_it=max_it, eps=eps, block=block, dot=dot)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    return min(times), info
+
+
+def cg_summary(args, edge=128):
+    """ACG on the variable-coefficient 7-point Poisson problem (edge^3 grid):
+    time to relative residual 1e-10 with qdot dots against FP64 dots."""
+    A, bd, nnz = cg_problem(edge)
+    timed_cg(A, bd, args.eps, args.block, "qdot")  # warm-up (graph instantiation, clocks)
+    t_q, iq = timed_cg(A, bd, args.eps, args.block, "qdot")
+    t_d, idd = timed_cg(A, bd, 1e-16, 0, "fp64")
+    return {"problem": f"7-point variable-coefficient Poisson {edge}^3 (n={A.n}, nnz={nnz}), coefficients "
+                       f"10^U(-3,3), rhs U(-1,1), x0 = 0, stop at ||r||/||b|| <= 1e-10",
+            "qdot": {"eps": args.eps, "block": args.block, "seconds": t_q, "iters": iq["iters"],
+                     "status": iq["status"], "true_relres": iq["true_relres"], "class_counts": list(iq["counts"])},
+            "fp64_dot": {"seconds": t_d, "iters": idd["iters"], "status": idd["status"],
+                         "true_relres": idd["true_relres"]},
+            "iters_equal": iq["iters"] == idd["iters"],
+            "time_ratio_qdot_over_fp64": t_q / t_d}
+
+
+def run_cg(args, rank, world, local, dist, lib):
+    """CG workload: one step = one ACG solve to 1e-10 (metric: seconds)."""
+    import torch
+    A, bd, nnz = cg_problem(args.grid)
+    for _ in range(max(args.warmup, 1)):
+        timed_cg(A, bd, args.eps, args.block, "qdot")
+    clocks = Clocks(local, not args.no_clocks)
+    dist.barrier()
+    times = []
+    info = None
+    for _ in range(args.steps):
+        t, info = timed_cg(A, bd, args.eps, args.block, "qdot")
+        times.append(t)
+    dist.barrier()
+    clk = clocks.stop()
+    t_mean = dist.max(statistics.mean(times))
+    t64, i64 = timed_cg(A, bd, 1e-16, 0, "fp64")
+    sweep = None
+    if args.eps_sweep:
+        sweep = []
+        for k in range(-16, 4):
+            for blk in (0, 32):
+                t, inf = timed_cg(A, bd, 10.0 ** k, blk, "qdot", max_it=60000)
+                sweep.append({"eps": 10.0 ** k, "block": blk, "iters": inf["iters"], "seconds": t,
+                              "status": inf["status"], "true_relres": inf["true_relres"],
+                              "class_counts": list(inf["counts"])})
+    n = A.n
+    # algorithmic bytes per iteration: CSR SpMV (12 B/nnz + 8 B/row pointer + 16 B/row for x, y)
+    # + 2 qdots (16 B/elem each) + x, r update (48 B/elem... read x p r q, write x r) + p update (24 B/elem)
+    it_bytes = 12 * nnz + 24 * n + 2 * 16 * n + 48 * n + 24 * n
+    its = info["iters"]
+    return {
+        "metric": "CG time-to-1e-10", "value": world / t_mean, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * t_mean,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"ACG (qdot dots) on the 7-point variable-coefficient Poisson {args.grid}^3 problem, "
+                               f"eps={args.eps:g}, block={args.block}, relative residual 1e-10",
+                   "n": n, "nnz": nnz, "l2": "matrix 190 MB > 129 MB L2 streamed every iteration"},
+        "seconds_to_1e-10": t_mean, "iters": its, "status": info["status"], "true_relres": info["true_relres"],
+        "us_per_iter": 1e6 * t_mean / max(its, 1),
+        "effective_gbs": it_bytes * its / t_mean / 1e9,
+        "fp64_dot_cg": {"seconds": t64, "iters": i64["iters"], "us_per_iter": 1e6 * t64 / max(i64["iters"], 1)},
+        "iters_equal_fp64": its == i64["iters"],
+        "eps_sweep": sweep, "cpu_baseline": None, "e2e": None, "clocks": clk,
+    }
+
+
+def run_power(args, rank, world, local, dist, lib):
+    """Power-method workload: 500 APM iterations on the 2048^2 5-point operator."""
+    import torch
+
+    import paper_2105_00115_gb300 as q
+    import workloads
+    rp, col, val = workloads.poisson2d(2048, 2048)
+    n = rp.shape[0] - 1
+    A = q.Csr(rp, col, val)
+    x0 = torch.from_numpy(workloads.unit_start(n)).cuda()
+
+    def solve(dot, eps, block):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lam, _, info, _ = q.power(A, x0, iters=500, eps=eps, block=block, dot=dot)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3, lam, info
+
+    for _ in range(max(args.warmup, 1)):
+        solve("qdot", args.eps, args.block)
+    clocks = Clocks(local, not args.no_clocks)
+    dist.barrier()
+    ts = []
+    for _ in range(args.steps):
+        t, lam, info = solve("qdot", args.eps, args.block)
+        ts.append(t)
+    dist.barrier()
+    clk = clocks.stop()
+    t_mean = dist.max(statistics.mean(ts))
+    t64, lam64, _ = solve("fp64", 1e-16, 0)
+    return {
+        "metric": "APM 500 iterations", "value": world / t_mean, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * t_mean,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"APM, 500 iterations, 5-point variable-coefficient operator 2048^2, "
+                               f"eps={args.eps:g}, block={args.block}", "n": n, "nnz": int(col.shape[0])},
+        "lambda": lam, "lambda_fp64_dot": lam64, "rel_diff": abs(lam - lam64) / abs(lam64),
+        "fp64_dot_seconds": t64, "class_counts": list(info["counts"]),
+        "cpu_baseline": None, "e2e": None, "clocks": clk,
+    }
+
+
+def run_backward(args, rank, world, local, dist, lib):
+    """Differentiation workload: 1024 pairs of length 2^16, loss sum_b qdot(x_b, y_b)^2,
+    one forward (batched launch) + backward per step."""
+    import torch
+
+    from paper_2105_00115_gb300 import autograd
+    Bn, L = 1024, 1 << 16
+    gen = torch.Generator(device="cuda").manual_seed(2105 + rank)
+
+    def lognormal():
+        m = torch.randn(Bn, L, generator=gen, device="cuda", dtype=torch.float64) * 4.0
+        sgn = torch.randint(0, 2, (Bn, L), generator=gen, device="cuda").to(torch.float64) * 2 - 1
+        return torch.exp(m) * sgn
+
+    X = lognormal().requires_grad_(True)
+    Y = lognormal().requires_grad_(True)
+
+    def step():
+        X.grad = None
+        Y.grad = None
+        z = autograd.qdot_batch_fn(X, Y, eps=args.eps, block=args.block)
+        (z * z).sum().backward()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local, not args.no_clocks)
+    dist.barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step()
+    t1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = dist.max(t0.elapsed_time(t1)) / args.steps
+    # forward 16 B/elem + backward 32 B/elem
+    total = Bn * L
+    return {
+        "metric": "qdot forward+backward GB/s", "value": world * 48.0 * total / (ms * 1e-3) / 1e9, "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"autograd qdot, 1024 pairs x 2^16, lognormal(sigma=4), loss sum z_b^2, "
+                               f"eps={args.eps:g}, block={args.block}",
+                   "l2": "inputs 1 GiB per step > 129 MB L2"},
+        "cpu_baseline": None, "e2e": None, "clocks": clk,
+    }
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -315,8 +504,9 @@ def main():
     torch.cuda.set_device(local)
     dist = Dist(world)
     lib = q.load()
-    if args.workload == "batched":
-        line = run_batched(args, rank, world, local, dist, lib)
+    if args.workload != "single":
+        fn = {"batched": run_batched, "cg": run_cg, "power": run_power, "backward": run_backward}[args.workload]
+        line = fn(args, rank, world, local, dist, lib)
         if rank == 0:
             print(json.dumps(line), flush=True)
         dist.close()
@@ -415,6 +605,10 @@ def main():
                "sample": f"first 2^{m.bit_length() - 1} of the 2^{n.bit_length() - 1} components of the same x, y "
                          f"({c_s:.1f} s, single thread)"}
 
+    cg = None
+    if not args.no_cg and rank == 0:
+        cg = cg_summary(args)
+
     peak, peak_src = measured_peak_hbm()
     kernel = "k_onepass" if lib.qdot_select_path(n, ctypes.byref(p), 1) == 2 else "k_apply"
     achieved = 16.0 * n / (kern_ms * 1e-3) / 1e9
@@ -429,6 +623,7 @@ def main():
         "pct_of_roofline": 100.0 * value / peak,
         "fp64_dot": {"value": dot_gbs, "unit": "GB/s", "ms": dot_ms, "frac": dot_gbs / peak,
                      "qdot_over_dot_time": (total_ms / args.steps) / dot_ms},
+        "cg": cg,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
         "clocks": clk,
         "result": {"value": res.value, "count": list(res.count), "n_bins": res.n_bins, "e_max": res.e_max,

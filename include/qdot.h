@@ -207,6 +207,34 @@ size_t qdot_power_workspace_size(int64_t n, const qdot_params* p);
 qdot_status qdot_power(const qdot_csr* A, double* x, int32_t iters, double tau, const qdot_params* p,
                        qdot_power_info* info, int64_t* class_hist, void* ws, size_t ws_bytes, void* stream);
 
+/* Backward of z = qdot(x, y) with the forward's class map held fixed (the
+ * classes of Algorithm 2, read straight-through): gx_i = g * q_c(y_i),
+ * gy_i = g * q_c(x_i) for components of class HALF / SINGLE / DOUBLE, +0 for
+ * PERF and ZERO.  The paper defines no derivative; this is the gradient of the
+ * frozen-class surrogate sum_i q_c(x_i) q_c(y_i) with each quantizer's
+ * derivative taken as 1.
+ *   x, y, n, p  the forward's operands and parameters (device, unchanged).
+ *   sel         device qdot_selection the forward qdot() wrote for them; each
+ *               component's class is re-derived from it and x, y.
+ *   g           device pointer to the upstream gradient dL/dz (one double).
+ *   gx, gy      device outputs of n doubles; either may be NULL.
+ * All device pointers 8-byte aligned (16 for 128-bit access).  Asynchronous;
+ * nothing is allocated. */
+qdot_status qdot_backward(const double* x, const double* y, int64_t n, const qdot_params* p,
+                          const qdot_selection* sel, const double* g, double* gx, double* gy, void* stream);
+
+/* Batched backward for qdot_batched() (blocked binning, 32 <= block <= 256):
+ * problem j's classes come from its forward result outs[j] (e_max, f) and
+ * x_j, y_j; gs[j] is dL/dz_j.  gxs / gys are device arrays of `count` device
+ * output pointers (either array may be NULL).  A problem whose forward status
+ * is not QDOT_OK gets NaN gradients.  Workspace:
+ * qdot_batched_backward_workspace_size(count) bytes, 256-byte aligned.
+ * grid_ctas: CTAs of the streaming kernel (0 = four per SM). */
+size_t qdot_batched_backward_workspace_size(int32_t count);
+qdot_status qdot_batched_backward(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
+                                  const qdot_params* p, const qdot_result* outs, const double* gs, double* const* gxs,
+                                  double* const* gys, int32_t grid_ctas, void* ws, size_t ws_bytes, void* stream);
+
 /* Plain FP64 dot product x.y (the comparator of the paper's speedup metric,
  * eq. approx-speedup): fused multiply-adds in a fixed order, written to
  * *out (device).  Workspace: qdot_dot_fp64_workspace_size(). */

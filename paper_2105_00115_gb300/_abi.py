@@ -65,6 +65,9 @@ SIGNATURES = {
     "qdot_explain": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "qdot_batched_workspace_size": (_SZ, [_VP, _I32, _PP]),
     "qdot_batched": (ctypes.c_int, [_VP, _VP, _VP, _I32, _PP, _VP, _I32, _VP, _SZ, _VP]),
+    "qdot_backward": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP]),
+    "qdot_batched_backward_workspace_size": (_SZ, [_I32]),
+    "qdot_batched_backward": (ctypes.c_int, [_VP, _VP, _VP, _I32, _PP, _VP, _VP, _VP, _VP, _I32, _VP, _SZ, _VP]),
     "qdot_cg_workspace_size": (_SZ, [_I64, _PP]),
     "qdot_cg": (ctypes.c_int, [_VP, _VP, _VP, _D, _I32, _PP, _VP, _VP, _VP, _SZ, _VP]),
     "qdot_power_workspace_size": (_SZ, [_I64, _PP]),
