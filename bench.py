@@ -522,13 +522,17 @@ def main():
     out = torch.empty(80, dtype=torch.uint8, device="cuda")
     launches = int(lib.qdot_kernel_launches(n, ctypes.byref(p), 1))
 
+    sel = torch.zeros(ctypes.sizeof(q.Selection), dtype=torch.uint8, device="cuda")
+
     def step():
-        q.qdot_async(xd, yd, args.eps, args.block, 1, 0, args.path, out=out, ws=ws, stream=stream)
+        q.qdot_async(xd, yd, args.eps, args.block, 1, 0, args.path, out=out, ws=ws, selection=sel, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     res = q.decode_result(out.cpu().numpy())
+    # blocks whose candidate the one-pass gather had to recompute
+    recomputed = q.Selection.from_buffer_copy(bytes(sel.cpu().numpy())).reserved[0]
 
     # timed region: K steps, per-step kernel events, clocks sampled meanwhile
     kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -627,7 +631,7 @@ def main():
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
         "clocks": clk,
         "result": {"value": res.value, "count": list(res.count), "n_bins": res.n_bins, "e_max": res.e_max,
-                   "f": res.f, "status": res.status},
+                   "f": res.f, "status": res.status, "recomputed_blocks": recomputed},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

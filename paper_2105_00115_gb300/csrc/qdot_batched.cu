@@ -4,9 +4,9 @@
 //
 //   k_bplan    one CTA: per-pair block and work-group counts, exclusive scans,
 //              argument checks (16-byte alignment, n >= 0), per-pair state.
-//   k_bstream  persistent: the warps split the concatenated work groups (8
-//              blocks each) of all pairs into equal contiguous ranges; every
-//              block's candidate sums go to a record as in the one-pass
+//   k_bstream  persistent: the warps split the concatenated warp items (256
+//              components each) of all pairs into equal contiguous ranges;
+//              every block's candidate sums go to a record as in the one-pass
 //              kernel; per-pair statistics are merged with one set of atomics
 //              per (warp, pair) run.
 //   k_bfinal   one CTA per pair: f = floor(log2(eps / N_bins)) exactly, the
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(1024) k_bplan(const double* const* __restrict_
     const bool ok = n >= 0 && (n == 0 || (aligned && xs[p] && ys[p]));
     const long long nb = ok ? ((n + (1ll << log2b) - 1) >> log2b) : 0;
     b += nb;
-    g += (nb + kBlocksPerWarp - 1) / kBlocksPerWarp;
+    g += ok ? (n + kItem - 1) / kItem : 0;
     PairStats s;
     s.e_max = kNone;
     s.e_min = INT_MAX;
@@ -85,9 +85,9 @@ __global__ void __launch_bounds__(1024) k_bplan(const double* const* __restrict_
     gpre[p] = go;
     bpre[p] = bo;
     const long long n = ns[p];
-    const long long nb = ps[p].status == QDOT_OK ? ((n + (1ll << log2b) - 1) >> log2b) : 0;
-    bo += nb;
-    go += (nb + kBlocksPerWarp - 1) / kBlocksPerWarp;
+    const bool ok = ps[p].status == QDOT_OK;
+    bo += ok ? ((n + (1ll << log2b) - 1) >> log2b) : 0;
+    go += ok ? (n + kItem - 1) / kItem : 0;
   }
   if (t == T - 1) {
     gpre[count] = s_g[T - 1];
@@ -113,7 +113,7 @@ __device__ __forceinline__ int find_pair(const long long* __restrict__ gpre, int
 }
 
 template <int LOG2B>
-__global__ void __launch_bounds__(kBThreads, 2) k_bstream(const double* const* __restrict__ xs,
+__global__ void __launch_bounds__(kBThreads, 3) k_bstream(const double* const* __restrict__ xs,
                                                           const double* const* __restrict__ ys,
                                                           const long long* __restrict__ ns, int count,
                                                           const long long* __restrict__ gpre,
@@ -121,19 +121,18 @@ __global__ void __launch_bounds__(kBThreads, 2) k_bstream(const double* const* _
                                                           PairStats* __restrict__ ps,
                                                           const BatchHeader* __restrict__ hdr,
                                                           BlockRec* __restrict__ recs) {
-  constexpr int kChunks = 1 << (LOG2B - 5);
+  constexpr int L = Map<LOG2B>::L, BPI = Map<LOG2B>::BPI;
   if (hdr->status != QDOT_OK) return;
   const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, sub = lane & 3;
-  const long long total = hdr->total_groups;
+  const int g = lane / L, sub = lane % L;
+  const long long total = hdr->total_groups;  // warp items over all pairs
   const long long gwarp = ((long long)blockIdx.x * kBThreads + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * kBThreads) >> 5;
   const long long per = (total + nwarps - 1) / nwarps;
   const long long g0 = min(total, gwarp * per), g1 = min(total, g0 + per);
   if (g0 >= g1) return;
 
-  // statistics of the current run of groups of one pair
-  int sp = find_pair(gpre, count, g0);
+  // statistics of the current run of items of one pair
   long long nbins = 0, zeros_l = 0;
   int emax_l = kNone, kmin = INT_MAX, bad = 0;
   auto flush = [&](int p) {
@@ -156,58 +155,43 @@ __global__ void __launch_bounds__(kBThreads, 2) k_bstream(const double* const* _
   };
 
   long long gg = g0;
-  int p = sp, c = 0;
+  int p = find_pair(gpre, count, g0);
   Chunk cur, nxt;
-  auto load_item = [&](long long item, int pp, int cc, Chunk& ch) {
-    const long long lg = item - gpre[pp];
-    load_chunk<LOG2B>(xs[pp], ys[pp], ns[pp], lg * kBlocksPerWarp + g, cc, sub, ch);
-  };
-  load_item(gg, p, 0, cur);
-  int u_run = kNone, M = 0, zeros = 0;
-  long long aH = 0, aS = 0;
-  double aD = 0.0;
+  load_item<LOG2B>(xs[p], ys[p], ns[p], gg - gpre[p], lane, cur);
   while (gg < g1) {
-    // next (group, chunk) of this warp, possibly in the next pair
-    long long ngg = gg;
-    int np = p, nc = c + 1;
-    if (nc == kChunks) {
-      nc = 0;
-      ++ngg;
-      while (np + 1 < count && ngg >= gpre[np + 1]) ++np;
-    }
-    if (ngg < g1) load_item(ngg, np, nc, nxt);
+    // next item of this warp, possibly in the next pair
+    const long long ngg = gg + 1;
+    int np = p;
+    while (np + 1 < count && ngg >= gpre[np + 1]) ++np;
+    if (ngg < g1) load_item<LOG2B>(xs[np], ys[np], ns[np], ngg - gpre[np], lane, nxt);
+    long long aH = 0, aS = 0;
+    double aD = 0.0;
+    int M = 0, zeros = 0, u;
     int key[8];
     int cmax = kNone;
     if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
-      chunk_fast<LOG2B>(cur, key, cmax, u_run, aH, aS, aD);
-      M += 8;
+      u = group_max<L>(cmax);
+      M = 8;
+      acc_fast<LOG2B, kCandAll>(cur, key, u, aH, aS, aD);
     } else {
-      chunk_general<LOG2B>(cur, u_run, aH, aS, aD, M, zeros, kmin, bad);
+      u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);
     }
-    if (c == kChunks - 1) {
-      int kb, u, mb;
-      const long long word = block_record_word<LOG2B>(aH, aS, aD, M, u_run, sub, &kb, &u, &mb);
-      const long long lb = (gg - gpre[p]) * kBlocksPerWarp + g;  // block index within pair p
-      const long long nblk_p = bpre[p + 1] - bpre[p];
-      zeros_l += zeros;
-      if (lb < nblk_p) {
-        if (mb > 0) {
-          nbins += (sub == 0);
-          emax_l = max(emax_l, u);
-        }
-        reinterpret_cast<long long*>(recs + bpre[p] + lb)[sub] = word;
+    int kb, ub, mb;
+    const long long word = block_record_word<LOG2B>(aH, aS, aD, M, u, kCandAll, sub, &kb, &ub, &mb);
+    const long long lb = (gg - gpre[p]) * BPI + g;  // block index within pair p
+    const long long nblk_p = bpre[p + 1] - bpre[p];
+    zeros_l += zeros;
+    if (lb < nblk_p) {
+      if (mb > 0) {
+        nbins += (sub == 0);
+        emax_l = max(emax_l, ub);
       }
-      u_run = kNone;
-      M = 0;
-      zeros = 0;
-      aH = aS = 0;
-      aD = 0.0;
-      if (np != p) flush(p);
+      if (sub < 4) reinterpret_cast<long long*>(recs + bpre[p] + lb)[sub] = word;
     }
+    if (np != p) flush(p);
     cur = nxt;
     gg = ngg;
     p = np;
-    c = nc;
   }
   flush(p < count ? p : count - 1);
 }
@@ -238,7 +222,7 @@ __global__ void __launch_bounds__(256) k_bfinal(const long long* __restrict__ ns
       const int key = (int)(short)(r1.y & 0xFFFF);
       if (key == kEmptyKey) continue;
       const int u = (int)(short)((r1.y >> 16) & 0xFFFF);
-      const unsigned m = (unsigned)((unsigned long long)r1.y >> 32);
+      const unsigned m = rec_count((unsigned)((unsigned long long)r1.y >> 32));
       const int cls = precision_of((long long)key - e_max - f + 1, mh, ms);
 #pragma unroll
       for (int k = 0; k < 4; ++k) c[k] += (cls == k) ? m : 0u;
@@ -365,7 +349,7 @@ qdot_status qdot_batched(const double* const* xs, const double* const* ys, const
     return QDOT_ERR_WORKSPACE;
   }
   const int sms = device_info().sms > 0 ? device_info().sms : 152;
-  const int grid = grid_ctas > 0 ? grid_ctas : 2 * sms;
+  const int grid = grid_ctas > 0 ? grid_ctas : 3 * sms;
   int lb = 0;
   while ((1 << lb) < p->block) ++lb;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

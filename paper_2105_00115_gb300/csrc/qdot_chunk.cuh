@@ -1,7 +1,15 @@
 // Per-block work shared by the one-pass kernels (single call and batched):
-// loading a 32-component chunk of a block, the exponent keys, and the exact
-// half / single / double candidate sums of the block (see qdot_onepass.cu for
-// the method and its error analysis).
+// loading a warp item of 256 components, the exponent keys, and the exact
+// half / single / double candidate sums of each block (see qdot_onepass.cu
+// for the method and its error analysis).
+//
+// Mapping.  A warp item is 256 consecutive components: 256 / B blocks of B
+// components, L = B / 8 lanes per block, 8 components per lane.  Lane l
+// serves block g = l / L of the item; its components are
+// g*B + 2*(l % L) + 2*L*j + {0, 1}, j = 0..3, read as four 16-byte loads of x
+// and of y.  The whole block is in registers at once, so its maximum key u_b
+// is known (a shuffle reduction over its L lanes) before any candidate is
+// accumulated.
 #pragma once
 
 #include <climits>
@@ -12,20 +20,29 @@ namespace qd {
 namespace chunk {
 
 constexpr int kNone = -(1 << 29);  // "no key" sentinel for component keys (biased by 2046)
-constexpr int kBlocksPerWarp = 8;  // blocks processed together by one warp (4 lanes each)
+constexpr int kItem = 256;         // components per warp item
 
-struct BlockRec {      // one per block, written by the block's 4 lanes
+// Candidate masks (bit = class number).
+constexpr unsigned kCandH = 1u << QDOT_HALF;
+constexpr unsigned kCandS = 1u << QDOT_SINGLE;
+constexpr unsigned kCandD = 1u << QDOT_DOUBLE;
+constexpr unsigned kCandAll = kCandH | kCandS | kCandD;
+
+struct BlockRec {      // one per block, written by 4 of the block's lanes
   long long h, s, d;   // candidate sums at LSB 2^(u_b - 60 + log2 B)
   short key, u;        // s_b and u_b (unbiased); key == kEmptyKey for an empty block
-  unsigned int m;      // M_b
+  unsigned int m;      // M_b in bits 0..15; the candidates present (kCand*) in bits 16..19
 };
 constexpr short kEmptyKey = -32768;
 
-// Per-component work of the streaming kernel, on 32-bit words.
+__device__ __forceinline__ unsigned rec_count(unsigned m) { return m & 0xFFFFu; }
+__device__ __forceinline__ unsigned rec_cands(unsigned m) { return m >> 16; }
+
+// Per-component work of the streaming kernels, on 32-bit words.
 //   x = (-1)^sx * mx:lx * 2^(e_x - 52): mx = top 21 bits of the 53-bit
 //   significand (implicit one at bit 20), lx = its low 32 bits.
-// With u the block's running maximum key (biased by 2046, like the component
-// keys) and d = u - e_i >= 0, the candidates at the block grid 2^(u - 60 + K):
+// With u the block's maximum key (biased by 2046, like the component keys)
+// and d = u - e_i >= 0, the candidates at the block grid 2^(u - 60 + K):
 //   H: q_half(x) q_half(y)    = Ph 2^(e_i - 20), Ph = Xh Yh  (|Ph| <= 2^22)
 //   S: q_single(x) q_single(y) = Ps 2^(e_i - 46), Ps = Xs Ys  (|Ps| <= 2^48)
 //   D: x y, on the FP64 pipe as (x / 2^e_x) (y / 2^(e_y + d)) with one fused
@@ -51,16 +68,31 @@ struct Chunk {
   bool valid[8];
 };
 
-// Load chunk c (32 components) of the lane group's block.
 template <int LOG2B>
-__device__ __forceinline__ void load_chunk(const double* __restrict__ x, const double* __restrict__ y, long long n,
-                                           long long blk, int c, int sub, Chunk& ch) {
-  const long long base = (blk << LOG2B) + c * 32 + sub * 2;
-  if (base - sub * 2 + 32 <= n) {
+struct Map {
+  static constexpr int L = 1 << (LOG2B - 3);  // lanes per block
+  static constexpr int BPI = kItem >> LOG2B;  // blocks per item
+};
+
+// Index of component j (0..7) of lane `lane` within its item.
+template <int LOG2B>
+__device__ __forceinline__ int item_offset(int lane, int j) {
+  constexpr int L = Map<LOG2B>::L;
+  return (lane / L) * (1 << LOG2B) + 2 * (lane % L) + 2 * L * (j >> 1) + (j & 1);
+}
+
+// Load warp item `item` of a vector pair of length n.
+template <int LOG2B>
+__device__ __forceinline__ void load_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                          long long item, int lane, Chunk& ch) {
+  constexpr int L = Map<LOG2B>::L;
+  const long long start = item * kItem;
+  const long long base = start + item_offset<LOG2B>(lane, 0);
+  if (start + kItem <= n) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const double2 a = __ldcs(reinterpret_cast<const double2*>(x + base + j * 8));
-      const double2 b = __ldcs(reinterpret_cast<const double2*>(y + base + j * 8));
+      const double2 a = __ldcs(reinterpret_cast<const double2*>(x + base + 2 * L * j));
+      const double2 b = __ldcs(reinterpret_cast<const double2*>(y + base + 2 * L * j));
       ch.x[2 * j] = (uint64_t)__double_as_longlong(a.x);
       ch.x[2 * j + 1] = (uint64_t)__double_as_longlong(a.y);
       ch.y[2 * j] = (uint64_t)__double_as_longlong(b.x);
@@ -70,7 +102,7 @@ __device__ __forceinline__ void load_chunk(const double* __restrict__ x, const d
   } else {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const long long i = base + (j >> 1) * 8 + (j & 1);
+      const long long i = start + item_offset<LOG2B>(lane, j);
       ch.valid[j] = i < n;
       ch.x[j] = ch.valid[j] ? (uint64_t)__double_as_longlong(x[i]) : 0ull;
       ch.y[j] = ch.valid[j] ? (uint64_t)__double_as_longlong(y[i]) : 0ull;
@@ -78,20 +110,82 @@ __device__ __forceinline__ void load_chunk(const double* __restrict__ x, const d
   }
 }
 
-__device__ __forceinline__ void rebase(int cmax, int& u_run, long long& aH, long long& aS, double& aD) {
-  if (cmax > u_run) {
-    if (u_run != kNone) {
-      const int dlt = min(cmax - u_run, 63);
-      aH >>= dlt;
-      aS >>= dlt;
-      aD = ldexp(aD, -dlt);
-    }
-    u_run = cmax;
+// ---------------------------------------------------------------------------
+// Shared-memory staging of warp items with cp.async (16-byte copies that hold
+// no registers while in flight).  Every lane copies its own 16-byte pieces
+// (pieces j = 0..3 of x, then of y) into a per-warp ring of kStages items laid
+// out [stage][array][j][lane], and later reads back exactly those pieces, so
+// no lane ever reads what another lane wrote.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 3;
+constexpr int kStageWords = 2 * 4 * 32;              // uint4 per stage
+constexpr int kRingBytes = kStages * kStageWords * 16;  // per warp: 12 KB
+
+__device__ __forceinline__ void cp_async16(uint4* dst, const void* src, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Start the copy of warp item `item` into one stage of the ring.  Pieces past
+// the end are zero-filled (a partial piece copies its in-range 8 bytes).
+template <int LOG2B>
+__device__ __forceinline__ void issue_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                           long long item, int lane, uint4* stage) {
+  constexpr int L = Map<LOG2B>::L;
+  const long long base = item * kItem + item_offset<LOG2B>(lane, 0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const long long i = base + 2 * L * j;
+    const int bytes = i + 2 <= n ? 16 : (i < n ? 8 : 0);
+    const long long src = bytes ? i : 0;  // an address inside x, y even when nothing is read
+    cp_async16(stage + j * 32 + lane, x + src, bytes);
+    cp_async16(stage + (4 + j) * 32 + lane, y + src, bytes);
   }
 }
 
-// Keys of a chunk and whether every component is present, finite, normal and
-// nonzero ("plain": the fast path applies).  Keys are biased by 2046.
+// Read a staged item back into registers.
+template <int LOG2B>
+__device__ __forceinline__ void read_item(const uint4* stage, long long n, long long item, int lane, Chunk& ch) {
+  const bool full = item * kItem + kItem <= n;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint4 a = stage[j * 32 + lane];
+    const uint4 b = stage[(4 + j) * 32 + lane];
+    ch.x[2 * j] = ((uint64_t)a.y << 32) | a.x;
+    ch.x[2 * j + 1] = ((uint64_t)a.w << 32) | a.z;
+    ch.y[2 * j] = ((uint64_t)b.y << 32) | b.x;
+    ch.y[2 * j + 1] = ((uint64_t)b.w << 32) | b.z;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) ch.valid[j] = full || item * kItem + item_offset<LOG2B>(lane, j) < n;
+}
+
+// Reductions over the L lanes of a block.
+template <int L>
+__device__ __forceinline__ int group_max(int v) {
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <int L>
+__device__ __forceinline__ long long group_sum(long long v) {
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int L>
+__device__ __forceinline__ int group_sum_i(int v) {
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Keys of a lane's components and whether every component is present,
+// finite, normal and nonzero ("plain": the fast path applies).  Keys are
+// biased by 2046.  kmin is updated only on the plain path.
 __device__ __forceinline__ bool chunk_keys(const Chunk& ch, int (&key)[8], int& cmax, int& kmin) {
   uint32_t amin = 0xFFFFFFFFu, amax = 0u;
   bool all_valid = true;
@@ -113,35 +207,86 @@ __device__ __forceinline__ bool chunk_keys(const Chunk& ch, int (&key)[8], int& 
   return plain;
 }
 
-template <int LOG2B>
-__device__ __forceinline__ void chunk_fast(const Chunk& ch, const int (&key)[8], int cmax, int& u_run,
-                                           long long& aH, long long& aS, double& aD) {
+// Candidates of the plain path for the classes in MASK, with u the block's
+// maximum key (biased).
+template <int LOG2B, unsigned MASK>
+__device__ __forceinline__ void acc_fast(const Chunk& ch, const int (&key)[8], int u, long long& aH, long long& aS,
+                                         double& aD) {
   constexpr int K = LOG2B;
-  cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, 1));
-  cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, 2));
-  rebase(cmax, u_run, aH, aS, aD);
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint32_t hx = (uint32_t)(ch.x[j] >> 32), lx = (uint32_t)ch.x[j];
     const uint32_t hy = (uint32_t)(ch.y[j] >> 32), ly = (uint32_t)ch.y[j];
-    const uint32_t mx = (hx & 0xFFFFFu) | 0x100000u, my = (hy & 0xFFFFFu) | 0x100000u;
-    const int sg = (int)(hx ^ hy) >> 31;  // 0 or -1
-    const int d = u_run - key[j];
-    const int sh = min(d, 63);
-    const int xh = (int)(half_sig(mx, lx) ^ (uint32_t)sg) - sg;
-    aH += ((long long)(xh * (int)half_sig(my, ly)) << (40 - K)) >> sh;
-    const int xs = (int)(single_sig(mx, lx) ^ (uint32_t)sg) - sg;
-    aS += (((long long)xs * (long long)single_sig(my, ly)) << (14 - K)) >> sh;
-    const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
-    aD = fma(make_double((hx & 0x800FFFFFu) | 0x3FF00000u, lx), make_double((hy & 0x800FFFFFu) | ye, ly), aD);
+    const int d = u - key[j];
+    if (MASK & (kCandH | kCandS)) {
+      const uint32_t mx = (hx & 0xFFFFFu) | 0x100000u, my = (hy & 0xFFFFFu) | 0x100000u;
+      const int sgn = ((int)(hx ^ hy) >> 31) | 1;  // +1 or -1
+      const int sh = min(d, 63);
+      if (MASK & kCandH) {
+        const int yh = (int)half_sig(my, ly) * sgn;
+        aH += ((long long)((int)half_sig(mx, lx) * yh) << (40 - K)) >> sh;
+      }
+      if (MASK & kCandS) {
+        const int ys = (int)single_sig(my, ly) * sgn;
+        aS += (((long long)(int)single_sig(mx, lx) * (long long)ys) << (14 - K)) >> sh;
+      }
+    }
+    if (MASK & kCandD) {
+      const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
+      aD = fma(make_double((hx & 0x800FFFFFu) | 0x3FF00000u, lx), make_double((hy & 0x800FFFFFu) | ye, ly), aD);
+    }
+  }
+}
+
+template <int LOG2B>
+__device__ __forceinline__ void acc_fast_mask(unsigned mask, const Chunk& ch, const int (&key)[8], int u,
+                                              long long& aH, long long& aS, double& aD) {
+  switch (mask >> 1) {  // warp-uniform
+    case 0: break;
+    case 1: acc_fast<LOG2B, kCandH>(ch, key, u, aH, aS, aD); break;
+    case 2: acc_fast<LOG2B, kCandS>(ch, key, u, aH, aS, aD); break;
+    case 3: acc_fast<LOG2B, kCandH | kCandS>(ch, key, u, aH, aS, aD); break;
+    case 4: acc_fast<LOG2B, kCandD>(ch, key, u, aH, aS, aD); break;
+    case 5: acc_fast<LOG2B, kCandH | kCandD>(ch, key, u, aH, aS, aD); break;
+    case 6: acc_fast<LOG2B, kCandS | kCandD>(ch, key, u, aH, aS, aD); break;
+    default: acc_fast<LOG2B, kCandAll>(ch, key, u, aH, aS, aD); break;
+  }
+}
+
+// Candidates of one component with key e (biased) in a block with maximum
+// key u (biased), any finite nonzero x, y given by their bits.
+template <int LOG2B>
+__device__ __forceinline__ void component_candidates(uint64_t xb, uint64_t yb, int e, int u, unsigned mask,
+                                                     long long& aH, long long& aS, double& aD) {
+  constexpr int K = LOG2B;
+  const uint64_t X = significand_of(xb), Y = significand_of(yb);
+  const uint32_t mx = (uint32_t)(X >> 32), lx = (uint32_t)X, my = (uint32_t)(Y >> 32), ly = (uint32_t)Y;
+  const int sgn = ((int)((uint32_t)(xb >> 32) ^ (uint32_t)(yb >> 32)) >> 31) | 1;
+  const int d = u - e;
+  const int sh = min(d, 63);
+  if (mask & kCandH) {
+    const int yh = (int)half_sig(my, ly) * sgn;
+    aH += ((long long)((int)half_sig(mx, lx) * yh) << (40 - K)) >> sh;
+  }
+  if (mask & kCandS) {
+    const int ys = (int)single_sig(my, ly) * sgn;
+    aS += (((long long)(int)single_sig(mx, lx) * (long long)ys) << (14 - K)) >> sh;
+  }
+  if (mask & kCandD) {
+    const uint32_t sx = (uint32_t)(xb >> 63), sy = (uint32_t)(yb >> 63);
+    const double xd = make_double((sx << 31) | 0x3FF00000u | (mx & 0xFFFFFu), lx);
+    const uint32_t ye = (uint32_t)(1023 - min(d, 1022)) << 20;
+    const double yd = make_double((sy << 31) | ye | (my & 0xFFFFFu), ly);
+    aD = fma(xd, yd, aD);
   }
 }
 
 // Any component: zeros, subnormals, non-finite values, or past the end.
+// Computes every candidate; returns the block maximum key (biased; kNone if
+// the block has no nonzero component) and adds the lane's counts.
 template <int LOG2B>
-__device__ __forceinline__ void chunk_general(const Chunk& ch, int& u_run, long long& aH, long long& aS, double& aD,
-                                              int& M, int& zeros, int& kmin, int& bad) {
-  constexpr int K = LOG2B;
+__device__ __forceinline__ int chunk_general(const Chunk& ch, long long& aH, long long& aS, double& aD, int& M,
+                                             int& zeros, int& kmin, int& bad) {
   int key[8];
   bool nz[8];
   int cmax = kNone;
@@ -158,43 +303,26 @@ __device__ __forceinline__ void chunk_general(const Chunk& ch, int& u_run, long 
     cmax = max(cmax, key[j]);
     if (nz[j]) kmin = min(kmin, key[j]);
   }
-  cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, 1));
-  cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, 2));
-  rebase(cmax, u_run, aH, aS, aD);
-  for (int j = 0; j < 8; ++j) {
-    if (!nz[j]) continue;
-    const uint64_t X = significand_of(ch.x[j]), Y = significand_of(ch.y[j]);
-    const uint32_t mx = (uint32_t)(X >> 32), lx = (uint32_t)X, my = (uint32_t)(Y >> 32), ly = (uint32_t)Y;
-    const int sg = (int)((uint32_t)(ch.x[j] >> 32) ^ (uint32_t)(ch.y[j] >> 32)) >> 31;
-    const int d = u_run - key[j];
-    const int sh = min(d, 63);
-    const int xh = (int)(half_sig(mx, lx) ^ (uint32_t)sg) - sg;
-    aH += ((long long)(xh * (int)half_sig(my, ly)) << (40 - K)) >> sh;
-    const int xs = (int)(single_sig(mx, lx) ^ (uint32_t)sg) - sg;
-    aS += (((long long)xs * (long long)single_sig(my, ly)) << (14 - K)) >> sh;
-    const uint32_t sx = (uint32_t)(ch.x[j] >> 63), sy = (uint32_t)(ch.y[j] >> 63);
-    const double xd = make_double((sx << 31) | 0x3FF00000u | (mx & 0xFFFFFu), lx);
-    const uint32_t ye = (uint32_t)(1023 - min(d, 1022)) << 20;
-    const double yd = make_double((sy << 31) | ye | (my & 0xFFFFFu), ly);
-    aD = fma(xd, yd, aD);
-  }
+  const int u = group_max<Map<LOG2B>::L>(cmax);
+  for (int j = 0; j < 8; ++j)
+    if (nz[j]) component_candidates<LOG2B>(ch.x[j], ch.y[j], key[j], u, kCandAll, aH, aS, aD);
+  return u;
 }
 
-
-// Block totals over the 4 lanes of a block, then the block's record word for
-// lane `sub` (0: H, 1: S, 2: D, 3: key / u / M).  u_run is biased by 2046.
+// Block totals over the L lanes of a block, then the block's record word
+// for lane sub = l % L < 4 (0: H, 1: S, 2: D, 3: key / u / M / candidates).
+// u is biased by 2046 (kNone for an empty block).
 template <int LOG2B>
-__device__ __forceinline__ long long block_record_word(long long aH, long long aS, double aD, int M, int u_run,
-                                                      int sub, int* key_out, int* u_out, int* m_out) {
+__device__ __forceinline__ long long block_record_word(long long aH, long long aS, double aD, int M, int u_b,
+                                                      unsigned cands, int sub, int* key_out, int* u_out,
+                                                      int* m_out) {
+  constexpr int L = Map<LOG2B>::L;
   long long aDi = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
-#pragma unroll
-  for (int o = 1; o <= 2; o <<= 1) {
-    aH += __shfl_xor_sync(0xffffffffu, aH, o);
-    aS += __shfl_xor_sync(0xffffffffu, aS, o);
-    aDi += __shfl_xor_sync(0xffffffffu, aDi, o);
-    M += __shfl_xor_sync(0xffffffffu, M, o);
-  }
-  const int u = u_run - 2046;
+  aH = group_sum<L>(aH);
+  aS = group_sum<L>(aS);
+  aDi = group_sum<L>(aDi);
+  M = group_sum_i<L>(M);
+  const int u = u_b - 2046;
   const int key = M > 0 ? ceil_log2_u32((uint32_t)M) + u : (int)kEmptyKey;
   *key_out = key;
   *u_out = u;
@@ -204,7 +332,60 @@ __device__ __forceinline__ long long block_record_word(long long aH, long long a
   if (sub == 2) return aDi;
   return (long long)(((unsigned long long)(uint16_t)(short)key) |
                      ((unsigned long long)(uint16_t)(short)(M > 0 ? u : 0) << 16) |
-                     ((unsigned long long)(unsigned)M << 32));
+                     ((unsigned long long)((unsigned)M | (cands << 16)) << 32));
+}
+
+// Compact record of one block (single-call path): two candidate slots and a
+// 32-bit meta word
+//   meta = (s_b + kMetaKeyBias) | M_b << 13 | (stored >> 1) << 22,  0 = empty block,
+// where `stored` (kCand* bits, at most two) names the candidates kept: the
+// higher class in slot 0, the other in slot 1.  u_b = s_b - ceil(log2 M_b).
+constexpr int kMetaKeyBias = 4096;
+
+template <int LOG2B>
+__device__ __forceinline__ void block_record_compact(long long aH, long long aS, double aD, int M, int u_b,
+                                                     unsigned stored, int sub, int* key_out, int* u_out,
+                                                     int* m_out, long long* slot, unsigned* meta) {
+  constexpr int L = Map<LOG2B>::L;
+  long long aDi = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
+  aH = group_sum<L>(aH);
+  aS = group_sum<L>(aS);
+  aDi = group_sum<L>(aDi);
+  M = group_sum_i<L>(M);
+  const int u = u_b - 2046;
+  const int key = M > 0 ? ceil_log2_u32((uint32_t)M) + u : (int)kEmptyKey;
+  *key_out = key;
+  *u_out = u;
+  *m_out = M;
+  long long hi, lo;
+  if (stored & kCandD) {
+    hi = aDi;
+    lo = (stored & kCandS) ? aS : aH;
+  } else if (stored & kCandS) {
+    hi = aS;
+    lo = aH;
+  } else {
+    hi = aH;
+    lo = 0;
+  }
+  *slot = sub == 0 ? hi : lo;
+  *meta = M > 0 ? ((unsigned)(key + kMetaKeyBias) | ((unsigned)M << 13) | ((stored >> 1) << 22)) : 0u;
+}
+
+__device__ __forceinline__ void unpack_meta(unsigned meta, int* key, int* u, unsigned* m, unsigned* stored) {
+  *key = (int)(meta & 0x1FFFu) - kMetaKeyBias;
+  *m = (meta >> 13) & 0x1FFu;
+  *stored = ((meta >> 22) & 7u) << 1;
+  *u = *key - ceil_log2_u32(*m);
+}
+
+// A block candidate at the grid 2^(u - 60 + log2 B), moved to the fixed-point
+// grid 2^lsb.
+__device__ __forceinline__ i128 candidate_to_fixed(long long v, int u, int log2b, int lsb) {
+  const int shift = (u - 60 + log2b) - lsb;
+  const i128 sv = (i128)v;
+  if (shift >= 0) return shift >= 127 ? (i128)0 : (sv << shift);
+  return (-shift) >= 127 ? (sv < 0 ? (i128)-1 : (i128)0) : (sv >> (-shift));
 }
 
 // Candidate of class cls from a record, moved from the block grid
@@ -217,6 +398,26 @@ __device__ __forceinline__ i128 record_candidate(long long h, long long s, long 
   i128 sv = (i128)v;
   if (shift >= 0) return shift >= 127 ? (i128)0 : (sv << shift);
   return (-shift) >= 127 ? (sv < 0 ? (i128)-1 : (i128)0) : (sv >> (-shift));
+}
+
+// The candidate of class cls of block blk, recomputed from x and y at the
+// record's grid (u unbiased): used when the streaming kernel skipped it.
+template <int LOG2B>
+__device__ long long recompute_candidate(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                         long long blk, int u, int cls) {
+  const long long lo = blk << LOG2B, hi = min(n, lo + (1ll << LOG2B));
+  long long aH = 0, aS = 0;
+  double aD = 0.0;
+  const unsigned mask = 1u << cls;
+  for (long long i = lo; i < hi; ++i) {
+    const uint64_t a = (uint64_t)__double_as_longlong(x[i]), b = (uint64_t)__double_as_longlong(y[i]);
+    if (is_zero(a) || is_zero(b)) continue;
+    const int e = exponent_of(a) + exponent_of(b) + 2046;
+    component_candidates<LOG2B>(a, b, e, u + 2046, mask, aH, aS, aD);
+  }
+  if (cls == kHalf) return aH;
+  if (cls == kSingle) return aS;
+  return __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
 }
 
 }  // namespace chunk

@@ -24,6 +24,7 @@
 // operands (relative error <= (B/4) 2^-53 per lane), then converted to the
 // same grid.
 #include <climits>
+#include <cmath>
 
 #include "qdot_chunk.cuh"
 #include "qdot_common.cuh"
@@ -36,6 +37,8 @@ using namespace chunk;
 
 constexpr int kOpThreads = 256;
 constexpr int kOpWarps = kOpThreads / 32;
+constexpr int kOpCtasPerSm = 2;                       // 2 x 96 KB of staging per SM
+constexpr int kOpSmem = kOpWarps * kRingBytes;
 
 // Per-warp record written to the workspace.
 struct WarpStats {
@@ -49,78 +52,140 @@ struct WarpStats {
 
 struct OpHeader {
   int L, lsb;
-  int status, pad;
+  int status;
+  int erun;            // running lower bound of e_max shared by the streaming warps (biased)
   long long zeros;
 };
 struct OpPart {
   i128 sum;
   unsigned long long cnt[4];
+  unsigned long long repairs;  // blocks whose candidate the gather recomputed
 };
 
 
+// Speculation windows: a block gets the SINGLE candidate when its score may
+// lie up to kWinS below its upper bound sigma_hi, the HALF candidate up to
+// kWinH below (HALF blocks are rare at practical eps, so its window is
+// narrow).  During the first 1/16 of a warp's items, while the running bound
+// of e_max still climbs fast, both windows widen by kWinEarly; a warp's first
+// two items get every candidate.
+constexpr int kWinS = 6, kWinH = 5, kWinEarly = 8;
+
+// The candidates a block with maximum key u (biased; kNone if empty) should
+// get, after folding u into the warp's running bound e_lo of e_max.  e_lo
+// also takes in erun, the bound shared by all warps: read at item 1 (used at
+// item 2), then every 16 items, each read used 16 items later so that it
+// completes while other items run.
 template <int LOG2B>
-__global__ void __launch_bounds__(kOpThreads, 2) k_onepass(const double* __restrict__ x,
-                                                           const double* __restrict__ y, long long n,
+__device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter, long long early_items, int f_spec,
+                                                      int mh, int ms, int* erun, int& e_lo, int& pending) {
+  constexpr int L = Map<LOG2B>::L;
+  int wmax = u;
+#pragma unroll
+  for (int o = L; o < 32; o <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if ((iter & 15) == 1) {
+    const int seen = __shfl_sync(0xffffffffu, pending, 0);  // loaded 16 items ago (none at the first read)
+    if (lane == 0) pending = *(volatile int*)erun;
+    e_lo = max(e_lo, seen);
+  }
+  if (iter == 2) e_lo = max(e_lo, __shfl_sync(0xffffffffu, pending, 0));  // the read issued at item 1
+  if (wmax > e_lo) {
+    e_lo = wmax;
+    if (lane == 0) atomicMax(erun, wmax);
+  }
+  if (u == kNone) return 0;
+  if (iter < 2) return kCandAll;  // before the first exchange e_lo is this warp's alone
+  // sigma_hi >= the block's score (e_lo <= e_max, f_spec <= f, ceil(log2 M_b) <= log2 B);
+  // candidates for the classes of scores in the window below sigma_hi
+  const int sig_hi = LOG2B + u - e_lo - f_spec + 1;
+  const int wide = iter < early_items ? kWinEarly : 0;
+  unsigned want = 0;
+  if (sig_hi >= ms) want |= kCandD;
+  if (sig_hi >= mh && sig_hi - kWinS - wide < ms) want |= kCandS;
+  if (sig_hi >= 0 && sig_hi - kWinH - wide < mh) want |= kCandH;
+  return want;
+}
+
+template <int LOG2B>
+__global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const double* __restrict__ x,
+                                                           const double* __restrict__ y, long long n, int f_spec,
+                                                           int mh, int ms, int* __restrict__ erun,
                                                            WarpStats* __restrict__ wstats,
-                                                           BlockRec* __restrict__ recs) {
-  constexpr long long B = 1ll << LOG2B;
-  constexpr int kChunks = (int)(B / 32);
+                                                           long long* __restrict__ slots,
+                                                           unsigned* __restrict__ metas) {
+  constexpr int L = Map<LOG2B>::L, BPI = Map<LOG2B>::BPI;
   const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, sub = lane & 3;
+  const int g = lane / L, sub = lane % L;
   long long nbins = 0, zeros_l = 0;
   int emax_l = kNone, kmin = INT_MAX, bad = 0;
 
-  const long long nblocks = (n + B - 1) / B;
-  const long long ngroups = (nblocks + kBlocksPerWarp - 1) / kBlocksPerWarp;
+  const long long nblocks = (n + (1ll << LOG2B) - 1) >> LOG2B;
+  const long long nitems = (n + kItem - 1) / kItem;
   const long long gwarp = ((long long)blockIdx.x * kOpThreads + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * kOpThreads) >> 5;
 
-  long long grp = gwarp;
-  int c = 0;
-  Chunk cur, nxt;
-  if (grp < ngroups) load_chunk<LOG2B>(x, y, n, grp * kBlocksPerWarp + g, 0, sub, cur);
-  int u_run = kNone, M = 0, zeros = 0;
-  long long aH = 0, aS = 0;
-  double aD = 0.0;
-  while (grp < ngroups) {
-    // prefetch the next chunk of this warp
-    long long ngrp = grp;
-    int nc = c + 1;
-    if (nc == kChunks) {
-      nc = 0;
-      ngrp = grp + nwarps;
+  int e_lo = kNone;     // lower bound of e_max (biased), the same in every lane
+  int pending = kNone;  // lane 0: the value erun held at its last read
+  int iter = 0;
+  const long long my_items = gwarp < nitems ? (nitems - gwarp + nwarps - 1) / nwarps : 0;
+  const long long early_items = (my_items + 15) / 16;
+  extern __shared__ uint4 s_ring[];
+  uint4* ring = s_ring + (threadIdx.x >> 5) * (kStages * kStageWords);
+  // prologue: items it, it + nwarps, ... (kStages - 1 of them) in flight
+#pragma unroll
+  for (int s = 0; s < kStages - 1; ++s) {
+    const long long item = gwarp + s * nwarps;
+    if (item < nitems) issue_item<LOG2B>(x, y, n, item, lane, ring + s * kStageWords);
+    cp_async_commit();
+  }
+  int stage = 0;
+  long long it = gwarp;
+  Chunk cur;
+  while (it < nitems) {
+    {  // refill the stage read in the previous iteration, kStages - 1 items ahead
+      const long long ahead = it + (long long)(kStages - 1) * nwarps;
+      const int st = stage == 0 ? kStages - 1 : stage - 1;
+      if (ahead < nitems) issue_item<LOG2B>(x, y, n, ahead, lane, ring + st * kStageWords);
+      cp_async_commit();
     }
-    if (ngrp < ngroups) load_chunk<LOG2B>(x, y, n, ngrp * kBlocksPerWarp + g, nc, sub, nxt);
+    cp_async_wait<kStages - 1>();  // this lane's copies of item `it` have landed
+    read_item<LOG2B>(ring + stage * kStageWords, n, it, lane, cur);
+    stage = stage == kStages - 1 ? 0 : stage + 1;
+    long long aH = 0, aS = 0;
+    double aD = 0.0;
+    int M = 0, zeros = 0, u;
+    unsigned want = 0;
     int key[8];
     int cmax = kNone;
     if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
-      chunk_fast<LOG2B>(cur, key, cmax, u_run, aH, aS, aD);
-      M += 8;
+      u = group_max<L>(cmax);
+      M = 8;
+      want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
+      acc_fast_mask<LOG2B>(__reduce_or_sync(0xffffffffu, want), cur, key, u, aH, aS, aD);
     } else {
-      chunk_general<LOG2B>(cur, u_run, aH, aS, aD, M, zeros, kmin, bad);
+      u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);  // every candidate
+      want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
     }
-    if (c == kChunks - 1) {
-      int key, u, mb;
-      const long long word = block_record_word<LOG2B>(aH, aS, aD, M, u_run, sub, &key, &u, &mb);
-      const long long blk = grp * kBlocksPerWarp + g;
-      zeros_l += zeros;
-      if (blk < nblocks) {
-        if (mb > 0) {
-          nbins += (sub == 0);
-          emax_l = max(emax_l, u);
-        }
-        reinterpret_cast<long long*>(recs + blk)[sub] = word;
+    // the record keeps at most two candidates: the block's highest wanted classes
+    const unsigned stored = want == kCandAll ? (kCandS | kCandD) : want;
+    int kb, ub, mb;
+    long long slot;
+    unsigned meta;
+    block_record_compact<LOG2B>(aH, aS, aD, M, u, stored, sub, &kb, &ub, &mb, &slot, &meta);
+    const long long blk = it * BPI + g;
+    zeros_l += zeros;
+    if (blk < nblocks) {
+      if (mb > 0) {
+        nbins += (sub == 0);
+        emax_l = max(emax_l, ub);
       }
-      u_run = kNone;
-      M = 0;
-      zeros = 0;
-      aH = aS = 0;
-      aD = 0.0;
+      if (sub < 2) slots[2 * blk + sub] = slot;
+      if (sub == 2) metas[blk] = meta;
     }
-    cur = nxt;
-    grp = ngrp;
-    c = nc;
+    it += nwarps;
+    ++iter;
   }
+  cp_async_wait<0>();
 
   // per-warp record
   emax_l = __reduce_max_sync(0xffffffffu, emax_l);
@@ -210,76 +275,117 @@ __global__ void __launch_bounds__(1024) k_op_select(const WarpStats* __restrict_
 
 // Deferred selection: per block record pick the candidate of the block's
 // class and add it exactly to a fixed-point sum anchored at 2^(e_max - L).
-__global__ void __launch_bounds__(256) k_op_gather(const BlockRec* __restrict__ recs, long long nblocks, int log2b,
+// A candidate the streaming kernel skipped is recomputed here from x and y.
+template <int LOG2B>
+__global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__ slots,
+                                                   const unsigned* __restrict__ metas, long long nblocks,
                                                    const qdot_selection* __restrict__ sel,
-                                                   const OpHeader* __restrict__ hdr, OpPart* __restrict__ parts) {
+                                                   const OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
+                                                   const double* __restrict__ x, const double* __restrict__ y,
+                                                   long long n) {
   __shared__ uint8_t s_lut[kKeyCount];
   __shared__ i128 s_sum[8];
-  __shared__ unsigned long long s_cnt[8][4];
+  __shared__ unsigned long long s_cnt[8][5];
   for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
     reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
   __syncthreads();
   const int lsb = hdr->lsb;
   const bool ok = hdr->status == QDOT_OK;
   i128 acc = 0;
-  unsigned long long c[4] = {0, 0, 0, 0};
-  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; ok && b < nblocks;
-       b += (long long)gridDim.x * blockDim.x) {
-    const longlong2 r0 = reinterpret_cast<const longlong2*>(recs + b)[0];
-    const longlong2 r1 = reinterpret_cast<const longlong2*>(recs + b)[1];
-    const int key = (int)(short)(r1.y & 0xFFFF);
-    if (key == kEmptyKey) continue;
-    const int u = (int)(short)((r1.y >> 16) & 0xFFFF);
-    const unsigned m = (unsigned)((unsigned long long)r1.y >> 32);
-    const int cls = s_lut[key - kKeyMin];
+  unsigned long long c[5] = {0, 0, 0, 0, 0};  // per class, then recomputed blocks
+  // four consecutive blocks per thread and step: one 16-byte load of their
+  // meta words, then the (independent) loads of the chosen candidates
+  const long long nquads = (nblocks + 3) >> 2;
+  for (long long qd4 = (long long)blockIdx.x * blockDim.x + threadIdx.x; ok && qd4 < nquads;
+       qd4 += (long long)gridDim.x * blockDim.x) {
+    const long long b0 = qd4 << 2;
+    unsigned mw[4];
+    if (b0 + 4 <= nblocks) {
+      const uint4 m4 = reinterpret_cast<const uint4*>(metas)[qd4];
+      mw[0] = m4.x;
+      mw[1] = m4.y;
+      mw[2] = m4.z;
+      mw[3] = m4.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) c[k] += (cls == k) ? m : 0u;
-    acc += record_candidate(r0.x, r0.y, r1.x, u, cls, log2b, lsb);
+      for (int k = 0; k < 4; ++k) mw[k] = b0 + k < nblocks ? metas[b0 + k] : 0u;
+    }
+    long long v[4];
+    int uu[4], cl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      cl[k] = kPerf;
+      uu[k] = 0;
+      v[k] = 0;
+      if (mw[k] == 0) continue;  // empty block
+      int key;
+      unsigned m, stored;
+      unpack_meta(mw[k], &key, &uu[k], &m, &stored);
+      const int cls = s_lut[key - kKeyMin];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) c[j] += (cls == j) ? m : 0u;
+      if (cls == kPerf) continue;
+      cl[k] = cls;
+      if (stored & (1u << cls)) {
+        const int top = 31 - __clz((int)stored);  // the highest stored class sits in slot 0
+        v[k] = slots[2 * (b0 + k) + (cls == top ? 0 : 1)];
+      } else {
+        v[k] = recompute_candidate<LOG2B>(x, y, n, b0 + k, uu[k], cls);
+        ++c[4];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (cl[k] != kPerf) acc += candidate_to_fixed(v[k], uu[k], LOG2B, lsb);
   }
   acc = warp_sum_i128(acc);
-  for (int k = 0; k < 4; ++k) c[k] = warp_sum_u64(c[k]);
+  for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     s_sum[w] = acc;
-    for (int k = 0; k < 4; ++k) s_cnt[w][k] = c[k];
+    for (int k = 0; k < 5; ++k) s_cnt[w][k] = c[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     OpPart p;
     p.sum = 0;
     for (int k = 0; k < 4; ++k) p.cnt[k] = 0;
+    p.repairs = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
       p.sum += s_sum[i];
       for (int k = 0; k < 4; ++k) p.cnt[k] += s_cnt[i][k];
+      p.repairs += s_cnt[i][4];
     }
     parts[blockIdx.x] = p;
   }
 }
 
 __global__ void __launch_bounds__(256) k_op_final(const OpPart* __restrict__ parts, int np,
-                                                  const qdot_selection* __restrict__ sel,
+                                                  qdot_selection* __restrict__ sel,
                                                   const OpHeader* __restrict__ hdr, qdot_result* __restrict__ out) {
   __shared__ i128 s_sum[8];
-  __shared__ unsigned long long s_cnt[8][4];
+  __shared__ unsigned long long s_cnt[8][5];
   i128 acc = 0;
-  unsigned long long c[4] = {0, 0, 0, 0};
+  unsigned long long c[5] = {0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < np; i += blockDim.x) {
     acc += parts[i].sum;
     for (int k = 0; k < 4; ++k) c[k] += parts[i].cnt[k];
+    c[4] += parts[i].repairs;
   }
   acc = warp_sum_i128(acc);
-  for (int k = 0; k < 4; ++k) c[k] = warp_sum_u64(c[k]);
+  for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     s_sum[w] = acc;
-    for (int k = 0; k < 4; ++k) s_cnt[w][k] = c[k];
+    for (int k = 0; k < 5; ++k) s_cnt[w][k] = c[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
       acc += s_sum[i];
-      for (int k = 0; k < 4; ++k) c[k] += s_cnt[i][k];
+      for (int k = 0; k < 5; ++k) c[k] += s_cnt[i][k];
     }
+    sel->reserved[0] = (int32_t)(c[4] < 0x7FFFFFFFull ? c[4] : 0x7FFFFFFFull);
     qdot_result r;
     r.status = hdr->status;
     r.n_bins = sel->n_bins;
@@ -299,25 +405,47 @@ __global__ void __launch_bounds__(256) k_op_final(const OpPart* __restrict__ par
   }
 }
 
+// The largest k with N * 2^k <= eps (host side; only steers which candidates
+// the streaming kernel computes, so an off-by-one costs time, not accuracy).
+int host_floor_log2_ratio(double eps, unsigned long long N) {
+  const double dn = (double)N;
+  int k = std::ilogb(eps) - std::ilogb(dn);
+  for (int i = 0; i < 4 && std::ldexp(dn, k) > eps; ++i) --k;
+  for (int i = 0; i < 4 && std::ldexp(dn, k + 1) <= eps; ++i) ++k;
+  return k;
+}
+
 template <int LOG2B>
 cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_params* p, const OnePassPlan& pl,
                       char* ws, qdot_result* out, cudaStream_t st) {
   auto* sel = reinterpret_cast<qdot_selection*>(ws + pl.off_sel);
   auto* hdr = reinterpret_cast<OpHeader*>(ws + pl.off_hdr);
   auto* wst = reinterpret_cast<WarpStats*>(ws + pl.off_rec);
-  auto* recs = reinterpret_cast<BlockRec*>(ws + pl.off_misc);
+  auto* slots = reinterpret_cast<long long*>(ws + pl.off_misc);
+  auto* metas = reinterpret_cast<unsigned*>(ws + pl.off_meta);
   auto* parts = reinterpret_cast<OpPart*>(ws + pl.off_sel + align_up(sizeof(qdot_selection), 256) +
                                           align_up(sizeof(OpHeader), 256));
+  const long long nblocks = (n + (1ll << LOG2B) - 1) >> LOG2B;
+  // f if every block is non-empty (a lower bound of the real f)
+  const int f_spec = host_floor_log2_ratio(p->eps, p->split_budget ? (unsigned long long)nblocks : 1ull);
+  const int mh = p->mant_reading ? 11 : 10, ms = p->mant_reading ? 24 : 23;
+  cudaError_t e = cudaMemsetAsync(&hdr->erun, 0x80, sizeof(int), st);  // very negative
+  if (e != cudaSuccess) return e;
   cudaEvent_t ev0, ev1;
   kernel_events(&ev0, &ev1);
   if (ev0) cudaEventRecord(ev0, st);
-  k_onepass<LOG2B><<<pl.grid, kOpThreads, 0, st>>>(x, y, n, wst, recs);
+  static bool smem_set = false;  // per instantiation
+  if (!smem_set) {
+    e = cudaFuncSetAttribute(k_onepass<LOG2B>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOpSmem);
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
+  k_onepass<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, slots, metas);
   if (ev1) cudaEventRecord(ev1, st);
   const int nw = pl.grid * kOpWarps;
   k_op_select<<<1, 1024, 0, st>>>(wst, nw, n, *p, sel, hdr);
   const int gather_grid = 4 * (device_info().sms > 0 ? device_info().sms : 152);
-  const long long nblocks = (n + (1ll << LOG2B) - 1) >> LOG2B;
-  k_op_gather<<<gather_grid, 256, 0, st>>>(recs, nblocks, LOG2B, sel, hdr, parts);
+  k_op_gather<LOG2B><<<gather_grid, 256, 0, st>>>(slots, metas, nblocks, sel, hdr, parts, x, y, n);
   k_op_final<<<1, 256, 0, st>>>(parts, gather_grid, sel, hdr, out);
   return cudaGetLastError();
 }
@@ -336,7 +464,7 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
   while ((1 << lb) < p->block) ++lb;
   pl.log2b = lb;
   const int sms = device_info().sms > 0 ? device_info().sms : 152;
-  pl.grid = sms * 2;
+  pl.grid = sms * kOpCtasPerSm;
   const long long nblocks = (n + p->block - 1) / p->block;
   size_t off = 0;
   pl.off_sel = off;
@@ -346,8 +474,10 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
   off = align_up(off + sizeof(OpPart) * 4 * sms, 256);  // gather partials
   pl.off_rec = off;
   off = align_up(off + sizeof(WarpStats) * pl.grid * kOpWarps, 256);
-  pl.off_misc = off;
-  off = align_up(off + sizeof(BlockRec) * (size_t)nblocks, 256);
+  pl.off_misc = off;  // two candidate slots per block
+  off = align_up(off + 2 * sizeof(long long) * (size_t)nblocks, 256);
+  pl.off_meta = off;  // one meta word per block
+  off = align_up(off + sizeof(unsigned) * (size_t)nblocks, 256);
   pl.total = off;
   return pl;
 }

@@ -165,6 +165,61 @@ def test_from_host_end_to_end(q, orc):
     assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
 
 
+def _repairs(q, x, y, eps, block):
+    """(result, blocks whose candidate the gather recomputed) of one-pass qdot."""
+    import ctypes
+    import torch
+    sel = torch.zeros(ctypes.sizeof(q.Selection), dtype=torch.uint8, device="cuda")
+    out = q.qdot_async(_dev(x), _dev(y), eps=eps, block=block, path="one_pass", selection=sel)
+    r = q.decode_result(out.cpu().numpy())
+    s = q.Selection.from_buffer_copy(bytes(sel.cpu().numpy()))
+    return r, s.reserved[0]
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+@pytest.mark.parametrize("eps", [1e-15, 1e-8, 1e-3, 10.0])
+def test_one_pass_skipped_candidates_recomputed(q, orc, block, eps):
+    """Inputs whose magnitudes grow along the vector: the streaming kernel's
+    running bound of e_max lags, it skips candidates the final classes need,
+    and the gather recomputes them.  Results must still match the oracle."""
+    n = (1 << 20) + 77
+    x, y = workloads.pair("a", n, 91)
+    ramp = np.exp2(np.linspace(0.0, 60.0, n))
+    x = x * ramp
+    r, rep = _repairs(q, x, y, eps, block)
+    ref = orc.qdot(x, y, eps=eps, block=block)
+    assert r.count == tuple(ref.count)
+    assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
+    assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
+    # a shuffled copy of the same components needs (almost) no recomputation
+    perm = np.random.default_rng(3).permutation(n)
+    r2, rep2 = _repairs(q, x[perm], y[perm], eps, block)
+    ref2 = orc.qdot(x[perm], y[perm], eps=eps, block=block)
+    assert r2.count == tuple(ref2.count)
+    assert abs(r2.value - ref2.value) <= TOL * orc.abs_dot_exact(x, y)
+    assert rep2 <= rep
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_one_pass_recompute_path(q, orc, block):
+    """A ramp 2^0 .. 2^40 whose last component is 2^60: until the end every
+    block looks DOUBLE to the streaming kernel, but the final e_max makes the
+    blocks with u_b in [12, 35) HALF or SINGLE, so the gather must recompute
+    those candidates."""
+    n = (1 << 20) + 77
+    rng = np.random.default_rng(17)
+    x = np.exp2(np.linspace(0.0, 40.0, n)) * rng.uniform(1.0, 2.0, n)
+    x[-1] = 2.0**60
+    y = rng.uniform(1.0, 2.0, n) * rng.choice([-1.0, 1.0], n)
+    r, rep = _repairs(q, x, y, 1e-8, block)
+    ref = orc.qdot(x, y, eps=1e-8, block=block)
+    assert rep > 0
+    assert r.count[1] > 0 and r.count[2] > 0
+    assert r.count == tuple(ref.count)
+    assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
+    assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
+
+
 def test_deterministic_repeat(q, orc):
     x, y = workloads.pair("c", 1 << 20, 5)
     xd, yd = _dev(x), _dev(y)
