@@ -42,11 +42,17 @@ __device__ __forceinline__ unsigned rec_cands(unsigned m) { return m >> 16; }
 //   x = (-1)^sx * mx:lx * 2^(e_x - 52): mx = top 21 bits of the 53-bit
 //   significand (implicit one at bit 20), lx = its low 32 bits.
 // With u the block's maximum key (biased by 2046, like the component keys)
-// and d = u - e_i >= 0, the candidates at the block grid 2^(u - 60 + K):
-//   H: q_half(x) q_half(y)    = Ph 2^(e_i - 20), Ph = Xh Yh  (|Ph| <= 2^22)
-//   S: q_single(x) q_single(y) = Ps 2^(e_i - 46), Ps = Xs Ys  (|Ps| <= 2^48)
+// and d = u - e_i >= 0, the candidates as integers on a per-block grid:
+//   H: q_half(x) q_half(y)    = Ph 2^(e_i - 20), Ph = Xh Yh  (|Ph| <= 2^22),
+//      grid 2^(u - 60 + K)
+//   S: q_single(x) q_single(y) = Ps 2^(e_i - 46), Ps = Xs Ys  (|Ps| <= 2^48),
+//      grid 2^(u - 52): the term is (Xs * (Ys * 64)) >> d, the 2^6 folded
+//      into the 32-bit operand of one widening multiply
 //   D: x y, on the FP64 pipe as (x / 2^e_x) (y / 2^(e_y + d)) with one fused
-//      multiply-add per component (exact operands).
+//      multiply-add per component (exact operands), grid 2^(u - 60 + K).
+// Every term is below 2^(62 - K), so a block's sum fits in 64 bits; the
+// truncation costs at most one grid unit per component, a relative error of
+// at most B 2^-52 <= 2^-44 of the block's sum of |x_i y_i|.
 
 // Round the 53-bit significand mx:lx to 11 bits (ties to even).
 __device__ __forceinline__ uint32_t half_sig(uint32_t mx, uint32_t lx) {
@@ -59,13 +65,31 @@ __device__ __forceinline__ uint32_t single_sig(uint32_t mx, uint32_t lx) {
   return keep + (((lx & 0x1FFFFFFFu) + 0x0FFFFFFFu + (keep & 1u)) >> 29);
 }
 
+// Arithmetic shift right; amounts of 64 and more give the sign (PTX clamps).
+__device__ __forceinline__ long long sar64(long long v, int s) {
+  long long r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(s));
+  return r;
+}
+
+// +1 or -1: the sign of x y from the high words of x and y.
+__device__ __forceinline__ int product_sign(uint32_t hx, uint32_t hy) {
+  return (int)((hx ^ hy) | 0x7FFFFFFFu) >> 30;
+}
+
+// Exponent of the grid of candidate class cls for a block with maximum key u
+// (unbiased) and blocks of 2^log2b.
+__device__ __forceinline__ int candidate_grid(int cls, int u, int log2b) {
+  return cls == kSingle ? u - 52 : u - 60 + log2b;
+}
+
 __device__ __forceinline__ double make_double(uint32_t hi, uint32_t lo) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
 struct Chunk {
   uint64_t x[8], y[8];
-  bool valid[8];
+  unsigned vmask;  // bit j: component j lies inside the vector (0xFF for a full item)
 };
 
 template <int LOG2B>
@@ -97,15 +121,17 @@ __device__ __forceinline__ void load_item(const double* __restrict__ x, const do
       ch.x[2 * j + 1] = (uint64_t)__double_as_longlong(a.y);
       ch.y[2 * j] = (uint64_t)__double_as_longlong(b.x);
       ch.y[2 * j + 1] = (uint64_t)__double_as_longlong(b.y);
-      ch.valid[2 * j] = ch.valid[2 * j + 1] = true;
     }
+    ch.vmask = 0xFFu;
   } else {
+    ch.vmask = 0u;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const long long i = start + item_offset<LOG2B>(lane, j);
-      ch.valid[j] = i < n;
-      ch.x[j] = ch.valid[j] ? (uint64_t)__double_as_longlong(x[i]) : 0ull;
-      ch.y[j] = ch.valid[j] ? (uint64_t)__double_as_longlong(y[i]) : 0ull;
+      const bool in = i < n;
+      ch.vmask |= in ? (1u << j) : 0u;
+      ch.x[j] = in ? (uint64_t)__double_as_longlong(x[i]) : 0ull;
+      ch.y[j] = in ? (uint64_t)__double_as_longlong(y[i]) : 0ull;
     }
   }
 }
@@ -136,6 +162,14 @@ __device__ __forceinline__ void issue_item(const double* __restrict__ x, const d
                                            long long item, int lane, uint4* stage) {
   constexpr int L = Map<LOG2B>::L;
   const long long base = item * kItem + item_offset<LOG2B>(lane, 0);
+  if (item * kItem + kItem <= n) {  // the whole item is inside the vectors
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      cp_async16(stage + j * 32 + lane, x + base + 2 * L * j, 16);
+      cp_async16(stage + (4 + j) * 32 + lane, y + base + 2 * L * j, 16);
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const long long i = base + 2 * L * j;
@@ -149,18 +183,22 @@ __device__ __forceinline__ void issue_item(const double* __restrict__ x, const d
 // Read a staged item back into registers.
 template <int LOG2B>
 __device__ __forceinline__ void read_item(const uint4* stage, long long n, long long item, int lane, Chunk& ch) {
-  const bool full = item * kItem + kItem <= n;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const uint4 a = stage[j * 32 + lane];
-    const uint4 b = stage[(4 + j) * 32 + lane];
-    ch.x[2 * j] = ((uint64_t)a.y << 32) | a.x;
-    ch.x[2 * j + 1] = ((uint64_t)a.w << 32) | a.z;
-    ch.y[2 * j] = ((uint64_t)b.y << 32) | b.x;
-    ch.y[2 * j + 1] = ((uint64_t)b.w << 32) | b.z;
+    const ulonglong2 a = reinterpret_cast<const ulonglong2*>(stage)[j * 32 + lane];
+    const ulonglong2 b = reinterpret_cast<const ulonglong2*>(stage)[(4 + j) * 32 + lane];
+    ch.x[2 * j] = a.x;
+    ch.x[2 * j + 1] = a.y;
+    ch.y[2 * j] = b.x;
+    ch.y[2 * j + 1] = b.y;
   }
+  if (item * kItem + kItem <= n) {
+    ch.vmask = 0xFFu;
+  } else {
+    ch.vmask = 0u;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) ch.valid[j] = full || item * kItem + item_offset<LOG2B>(lane, j) < n;
+    for (int j = 0; j < 8; ++j) ch.vmask |= item * kItem + item_offset<LOG2B>(lane, j) < n ? (1u << j) : 0u;
+  }
 }
 
 // Reductions over the L lanes of a block.
@@ -188,18 +226,16 @@ __device__ __forceinline__ int group_sum_i(int v) {
 // biased by 2046.  kmin is updated only on the plain path.
 __device__ __forceinline__ bool chunk_keys(const Chunk& ch, int (&key)[8], int& cmax, int& kmin) {
   uint32_t amin = 0xFFFFFFFFu, amax = 0u;
-  bool all_valid = true;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint32_t ax = (uint32_t)(ch.x[j] >> 32) & 0x7FF00000u, ay = (uint32_t)(ch.y[j] >> 32) & 0x7FF00000u;
     amin = min(amin, min(ax, ay));
     amax = max(amax, max(ax, ay));
-    all_valid &= ch.valid[j];
     key[j] = (int)((ax + ay) >> 20);
     cmax = max(cmax, key[j]);
   }
   // exponent fields in [1, 2046] on both sides: no zero, subnormal, Inf or NaN
-  const bool plain = all_valid && amin != 0u && amax != 0x7FF00000u;
+  const bool plain = ch.vmask == 0xFFu && amin != 0u && amax != 0x7FF00000u;
   if (plain) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) kmin = min(kmin, key[j]);
@@ -220,15 +256,14 @@ __device__ __forceinline__ void acc_fast(const Chunk& ch, const int (&key)[8], i
     const int d = u - key[j];
     if (MASK & (kCandH | kCandS)) {
       const uint32_t mx = (hx & 0xFFFFFu) | 0x100000u, my = (hy & 0xFFFFFu) | 0x100000u;
-      const int sgn = ((int)(hx ^ hy) >> 31) | 1;  // +1 or -1
-      const int sh = min(d, 63);
+      const int sgn = product_sign(hx, hy);
       if (MASK & kCandH) {
         const int yh = (int)half_sig(my, ly) * sgn;
-        aH += ((long long)((int)half_sig(mx, lx) * yh) << (40 - K)) >> sh;
+        aH += sar64((long long)((int)half_sig(mx, lx) * yh) << (40 - K), d);
       }
       if (MASK & kCandS) {
-        const int ys = (int)single_sig(my, ly) * sgn;
-        aS += (((long long)(int)single_sig(mx, lx) * (long long)ys) << (14 - K)) >> sh;
+        const int ys = (int)single_sig(my, ly) * (sgn * 64);
+        aS += sar64((long long)(int)single_sig(mx, lx) * (long long)ys, d);
       }
     }
     if (MASK & kCandD) {
@@ -261,16 +296,15 @@ __device__ __forceinline__ void component_candidates(uint64_t xb, uint64_t yb, i
   constexpr int K = LOG2B;
   const uint64_t X = significand_of(xb), Y = significand_of(yb);
   const uint32_t mx = (uint32_t)(X >> 32), lx = (uint32_t)X, my = (uint32_t)(Y >> 32), ly = (uint32_t)Y;
-  const int sgn = ((int)((uint32_t)(xb >> 32) ^ (uint32_t)(yb >> 32)) >> 31) | 1;
+  const int sgn = product_sign((uint32_t)(xb >> 32), (uint32_t)(yb >> 32));
   const int d = u - e;
-  const int sh = min(d, 63);
   if (mask & kCandH) {
     const int yh = (int)half_sig(my, ly) * sgn;
-    aH += ((long long)((int)half_sig(mx, lx) * yh) << (40 - K)) >> sh;
+    aH += sar64((long long)((int)half_sig(mx, lx) * yh) << (40 - K), d);
   }
   if (mask & kCandS) {
-    const int ys = (int)single_sig(my, ly) * sgn;
-    aS += (((long long)(int)single_sig(mx, lx) * (long long)ys) << (14 - K)) >> sh;
+    const int ys = (int)single_sig(my, ly) * (sgn * 64);
+    aS += sar64((long long)(int)single_sig(mx, lx) * (long long)ys, d);
   }
   if (mask & kCandD) {
     const uint32_t sx = (uint32_t)(xb >> 63), sy = (uint32_t)(yb >> 63);
@@ -293,11 +327,12 @@ __device__ __forceinline__ int chunk_general(const Chunk& ch, long long& aH, lon
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint64_t a = ch.x[j], b = ch.y[j];
+    const bool in = (ch.vmask >> j) & 1u;
     const bool fin = !(is_nonfinite(a) || is_nonfinite(b));
-    bad |= ch.valid[j] && !fin;
+    bad |= in && !fin;
     const bool z = is_zero(a) || is_zero(b);
-    nz[j] = ch.valid[j] && fin && !z;
-    zeros += ch.valid[j] && fin && z;
+    nz[j] = in && fin && !z;
+    zeros += in && fin && z;
     M += nz[j];
     key[j] = nz[j] ? exponent_of(a) + exponent_of(b) + 2046 : kNone;  // biased like the fast path
     cmax = max(cmax, key[j]);
@@ -338,14 +373,17 @@ __device__ __forceinline__ long long block_record_word(long long aH, long long a
 // Compact record of one block (single-call path): two candidate slots and a
 // 32-bit meta word
 //   meta = (s_b + kMetaKeyBias) | M_b << 13 | (stored >> 1) << 22,  0 = empty block,
-// where `stored` (kCand* bits, at most two) names the candidates kept: the
-// higher class in slot 0, the other in slot 1.  u_b = s_b - ceil(log2 M_b).
+// where `stored` (kCand* bits) names the candidates kept: the higher class in
+// slot 0, the next in slot 1; when all three are kept (a warp's first items)
+// the HALF candidate goes to a third, short array indexed by block.
+// u_b = s_b - ceil(log2 M_b).
 constexpr int kMetaKeyBias = 4096;
 
 template <int LOG2B>
 __device__ __forceinline__ void block_record_compact(long long aH, long long aS, double aD, int M, int u_b,
                                                      unsigned stored, int sub, int* key_out, int* u_out,
-                                                     int* m_out, long long* slot, unsigned* meta) {
+                                                     int* m_out, long long* slot, unsigned* meta,
+                                                     long long* half_out) {
   constexpr int L = Map<LOG2B>::L;
   long long aDi = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
   aH = group_sum<L>(aH);
@@ -357,6 +395,7 @@ __device__ __forceinline__ void block_record_compact(long long aH, long long aS,
   *key_out = key;
   *u_out = u;
   *m_out = M;
+  *half_out = aH;
   long long hi, lo;
   if (stored & kCandD) {
     hi = aDi;
@@ -379,22 +418,22 @@ __device__ __forceinline__ void unpack_meta(unsigned meta, int* key, int* u, uns
   *u = *key - ceil_log2_u32(*m);
 }
 
-// A block candidate at the grid 2^(u - 60 + log2 B), moved to the fixed-point
-// grid 2^lsb.
-__device__ __forceinline__ i128 candidate_to_fixed(long long v, int u, int log2b, int lsb) {
-  const int shift = (u - 60 + log2b) - lsb;
+// A block candidate of class cls on its grid, moved to the fixed-point grid
+// 2^lsb.
+__device__ __forceinline__ i128 candidate_to_fixed(long long v, int cls, int u, int log2b, int lsb) {
+  const int shift = candidate_grid(cls, u, log2b) - lsb;
   const i128 sv = (i128)v;
   if (shift >= 0) return shift >= 127 ? (i128)0 : (sv << shift);
   return (-shift) >= 127 ? (sv < 0 ? (i128)-1 : (i128)0) : (sv >> (-shift));
 }
 
-// Candidate of class cls from a record, moved from the block grid
-// 2^(u - 60 + log2 B) to the fixed-point grid 2^lsb.
+// Candidate of class cls from a record, moved from its grid to the
+// fixed-point grid 2^lsb.
 __device__ __forceinline__ i128 record_candidate(long long h, long long s, long long d, int u, int cls, int log2b,
                                                  int lsb) {
   if (cls == kPerf || cls == kZero) return 0;
   const long long v = cls == kHalf ? h : (cls == kSingle ? s : d);
-  const int shift = (u - 60 + log2b) - lsb;
+  const int shift = candidate_grid(cls, u, log2b) - lsb;
   i128 sv = (i128)v;
   if (shift >= 0) return shift >= 127 ? (i128)0 : (sv << shift);
   return (-shift) >= 127 ? (sv < 0 ? (i128)-1 : (i128)0) : (sv >> (-shift));

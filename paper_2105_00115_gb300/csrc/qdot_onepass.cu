@@ -23,6 +23,7 @@
 // pipe with one fused multiply-add per component on exponent-rescaled
 // operands (relative error <= (B/4) 2^-53 per lane), then converted to the
 // same grid.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 
@@ -112,7 +113,8 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
                                                            int mh, int ms, int* __restrict__ erun,
                                                            WarpStats* __restrict__ wstats,
                                                            long long* __restrict__ slots,
-                                                           unsigned* __restrict__ metas) {
+                                                           unsigned* __restrict__ metas,
+                                                           long long* __restrict__ slot3) {
   constexpr int L = Map<LOG2B>::L, BPI = Map<LOG2B>::BPI;
   const int lane = threadIdx.x & 31;
   const int g = lane / L, sub = lane % L;
@@ -166,12 +168,11 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
       u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);  // every candidate
       want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
     }
-    // the record keeps at most two candidates: the block's highest wanted classes
-    const unsigned stored = want == kCandAll ? (kCandS | kCandD) : want;
+    // the record keeps the block's wanted candidates
     int kb, ub, mb;
-    long long slot;
+    long long slot, half;
     unsigned meta;
-    block_record_compact<LOG2B>(aH, aS, aD, M, u, stored, sub, &kb, &ub, &mb, &slot, &meta);
+    block_record_compact<LOG2B>(aH, aS, aD, M, u, want, sub, &kb, &ub, &mb, &slot, &meta, &half);
     const long long blk = it * BPI + g;
     zeros_l += zeros;
     if (blk < nblocks) {
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
       }
       if (sub < 2) slots[2 * blk + sub] = slot;
       if (sub == 2) metas[blk] = meta;
+      if (sub == 3 && want == kCandAll && blk < 2 * nwarps * BPI) slot3[blk] = half;  // first two items only
     }
     it += nwarps;
     ++iter;
@@ -278,7 +280,9 @@ __global__ void __launch_bounds__(1024) k_op_select(const WarpStats* __restrict_
 // A candidate the streaming kernel skipped is recomputed here from x and y.
 template <int LOG2B>
 __global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__ slots,
-                                                   const unsigned* __restrict__ metas, long long nblocks,
+                                                   const unsigned* __restrict__ metas,
+                                                   const long long* __restrict__ slot3, long long n_early,
+                                                   long long nblocks,
                                                    const qdot_selection* __restrict__ sel,
                                                    const OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
                                                    const double* __restrict__ x, const double* __restrict__ y,
@@ -326,9 +330,11 @@ __global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__
       for (int j = 0; j < 4; ++j) c[j] += (cls == j) ? m : 0u;
       if (cls == kPerf) continue;
       cl[k] = cls;
+      if (stored == kCandAll && cls == kHalf && b0 + k >= n_early) stored = 0;  // never written
       if (stored & (1u << cls)) {
         const int top = 31 - __clz((int)stored);  // the highest stored class sits in slot 0
-        v[k] = slots[2 * (b0 + k) + (cls == top ? 0 : 1)];
+        v[k] = (stored == kCandAll && cls == kHalf) ? slot3[b0 + k]  // b0 + k < n_early by construction
+                                                    : slots[2 * (b0 + k) + (cls == top ? 0 : 1)];
       } else {
         v[k] = recompute_candidate<LOG2B>(x, y, n, b0 + k, uu[k], cls);
         ++c[4];
@@ -336,7 +342,7 @@ __global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (cl[k] != kPerf) acc += candidate_to_fixed(v[k], uu[k], LOG2B, lsb);
+      if (cl[k] != kPerf) acc += candidate_to_fixed(v[k], cl[k], uu[k], LOG2B, lsb);
   }
   acc = warp_sum_i128(acc);
   for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
@@ -423,6 +429,7 @@ cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_pa
   auto* wst = reinterpret_cast<WarpStats*>(ws + pl.off_rec);
   auto* slots = reinterpret_cast<long long*>(ws + pl.off_misc);
   auto* metas = reinterpret_cast<unsigned*>(ws + pl.off_meta);
+  auto* slot3 = reinterpret_cast<long long*>(ws + pl.off_slot3);
   auto* parts = reinterpret_cast<OpPart*>(ws + pl.off_sel + align_up(sizeof(qdot_selection), 256) +
                                           align_up(sizeof(OpHeader), 256));
   const long long nblocks = (n + (1ll << LOG2B) - 1) >> LOG2B;
@@ -440,12 +447,13 @@ cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_pa
     if (e != cudaSuccess) return e;
     smem_set = true;
   }
-  k_onepass<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, slots, metas);
+  k_onepass<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, slots, metas, slot3);
   if (ev1) cudaEventRecord(ev1, st);
   const int nw = pl.grid * kOpWarps;
   k_op_select<<<1, 1024, 0, st>>>(wst, nw, n, *p, sel, hdr);
   const int gather_grid = 4 * (device_info().sms > 0 ? device_info().sms : 152);
-  k_op_gather<LOG2B><<<gather_grid, 256, 0, st>>>(slots, metas, nblocks, sel, hdr, parts, x, y, n);
+  k_op_gather<LOG2B><<<gather_grid, 256, 0, st>>>(slots, metas, slot3, 2ll * pl.grid * kOpWarps * Map<LOG2B>::BPI,
+                                                    nblocks, sel, hdr, parts, x, y, n);
   k_op_final<<<1, 256, 0, st>>>(parts, gather_grid, sel, hdr, out);
   return cudaGetLastError();
 }
@@ -478,6 +486,9 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
   off = align_up(off + 2 * sizeof(long long) * (size_t)nblocks, 256);
   pl.off_meta = off;  // one meta word per block
   off = align_up(off + sizeof(unsigned) * (size_t)nblocks, 256);
+  pl.off_slot3 = off;  // HALF candidates of the blocks of every warp's first two items
+  const long long early_blocks = 2ll * pl.grid * kOpWarps * (kItem / p->block);
+  off = align_up(off + sizeof(long long) * (size_t)std::min(nblocks, early_blocks), 256);
   pl.total = off;
   return pl;
 }

@@ -205,8 +205,8 @@ def test_one_pass_recompute_path(q, orc, block):
     """A ramp 2^0 .. 2^40 whose last component is 2^60: until the end every
     block looks DOUBLE to the streaming kernel, but the final e_max makes the
     blocks with u_b in [12, 35) HALF or SINGLE, so the gather must recompute
-    those candidates."""
-    n = (1 << 20) + 77
+    those candidates (n large enough that each warp runs many items)."""
+    n = (1 << 24) + 77
     rng = np.random.default_rng(17)
     x = np.exp2(np.linspace(0.0, 40.0, n)) * rng.uniform(1.0, 2.0, n)
     x[-1] = 2.0**60
