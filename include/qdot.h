@@ -196,6 +196,23 @@ qdot_status qdot_cg(const qdot_csr* A, const double* b, double* x, double rel_to
                     const qdot_params* p, qdot_cg_info* info, int64_t* class_hist, void* ws, size_t ws_bytes,
                     void* stream);
 
+/* Batched ACG: `count` independent SPD systems solved together, each by
+ * Algorithm 4 with its own scalars and stopping test (as in qdot_cg).  A is
+ * one block-diagonal CSR matrix: system s owns rows (and columns)
+ * [row_off_host[s], row_off_host[s + 1]); a column outside its row's system
+ * is not used and makes every info[s].status QDOT_ERR_ARG.  b, x: device
+ * vectors of A->n doubles (x holds x0 on entry).  Each iteration is one SpMV
+ * launch, one batched-qdot launch per dot product and one launch per vector
+ * update over all systems; 16 iterations are replayed as one CUDA graph until
+ * every system has stopped.  p->block must lie in [32, 256] (the batched
+ * qdot); QDOT_PATH_FP64_DOT runs the plain-FP64-dot comparator.  infos:
+ * device array of `count` qdot_cg_info.  row_off_host is read during the call
+ * only.  Workspace: qdot_cg_batched_workspace_size(row_off_host, count, p). */
+size_t qdot_cg_batched_workspace_size(const int64_t* row_off_host, int32_t count, const qdot_params* p);
+qdot_status qdot_cg_batched(const qdot_csr* A, const int64_t* row_off_host, int32_t count, const double* b,
+                            double* x, double rel_tol, int32_t max_it, const qdot_params* p, qdot_cg_info* infos,
+                            void* ws, size_t ws_bytes, void* stream);
+
 /* APM, Algorithm 5 of the paper, with the eigenvalue estimate read as the
  * Rayleigh quotient: for k = 0, 1, ...: w = A x_k; lambda_k = qdot(x_k, w);
  * c = qdot(w, w); x_{k+1} = w * (1 / sqrt(c)); stop after `iters` iterations

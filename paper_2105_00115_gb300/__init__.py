@@ -16,7 +16,7 @@ from . import _abi
 from ._abi import Params, QdotError, Result, Selection, check, load
 
 __all__ = ["QdotResult", "QdotError", "qdot", "qdot_async", "explain", "dot_fp64", "from_host", "workspace_size",
-           "load", "params", "decode_result", "Batch", "Csr", "cg", "power"]
+           "load", "params", "decode_result", "Batch", "Csr", "cg", "cg_batched", "power"]
 
 CLASS_NAMES = ("perforate", "half", "single", "double", "zero")
 
@@ -260,6 +260,34 @@ def cg(A: Csr, b, x0=None, rel_tol=1e-10, max_it=50000, eps=1e-16, block=0, spli
            "counts": tuple(raw.counts)}
     h = hist[: raw.iters * 10].view(raw.iters, 2, 5).cpu().numpy() if history else None
     return x, out, h
+
+
+def cg_batched(A: Csr, row_off, b, x0=None, rel_tol=1e-10, max_it=50000, eps=1e-16, block=32, split_budget=1,
+               mant_reading=0, dot="qdot", stream=None):
+    """Batched ACG on the diagonal blocks of A (system s owns rows
+    [row_off[s], row_off[s+1])).  Returns (x, list of per-system info dicts)."""
+    torch = _torch()
+    lib = load()
+    _check_vec(b, "b")
+    ro = np.ascontiguousarray(row_off, dtype=np.int64)
+    count = ro.shape[0] - 1
+    x = torch.zeros_like(b) if x0 is None else x0.clone()
+    p = params(eps, block, split_budget, mant_reading, _solver_path(dot))
+    need = lib.qdot_cg_batched_workspace_size(ro.ctypes.data, count, ctypes.byref(p))
+    if need == 0:
+        raise QdotError(1, "invalid batched CG arguments (row offsets, or block outside [32, 256])")
+    ws = _workspace(need, b.device)
+    infos = torch.empty(max(count, 1) * 64, dtype=torch.uint8, device=b.device)
+    check(lib.qdot_cg_batched(ctypes.byref(A.abi), ro.ctypes.data, count, _ptr(b), _ptr(x), float(rel_tol),
+                              int(max_it), ctypes.byref(p), _ptr(infos), _ptr(ws), ws.numel(), _stream_ptr(stream)),
+          lib)
+    raw = bytes(infos.cpu().numpy())
+    out = []
+    for s in range(count):
+        r = _abi.CgInfo.from_buffer_copy(raw[64 * s: 64 * (s + 1)])
+        out.append({"iters": r.iters, "status": r.status, "relres": r.relres, "true_relres": r.true_relres,
+                    "counts": tuple(r.counts)})
+    return x, out
 
 
 def power(A: Csr, x0, iters=500, tau=0.0, eps=1e-16, block=0, split_budget=1, mant_reading=0, history=False,

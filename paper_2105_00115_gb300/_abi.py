@@ -70,6 +70,8 @@ SIGNATURES = {
     "qdot_batched_backward": (ctypes.c_int, [_VP, _VP, _VP, _I32, _PP, _VP, _VP, _VP, _VP, _I32, _VP, _SZ, _VP]),
     "qdot_cg_workspace_size": (_SZ, [_I64, _PP]),
     "qdot_cg": (ctypes.c_int, [_VP, _VP, _VP, _D, _I32, _PP, _VP, _VP, _VP, _SZ, _VP]),
+    "qdot_cg_batched_workspace_size": (_SZ, [_VP, _I32, _PP]),
+    "qdot_cg_batched": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP, _D, _I32, _PP, _VP, _VP, _SZ, _VP]),
     "qdot_power_workspace_size": (_SZ, [_I64, _PP]),
     "qdot_power": (ctypes.c_int, [_VP, _VP, _I32, _D, _PP, _VP, _VP, _VP, _SZ, _VP]),
     "qdot_dot_fp64_workspace_size": (_SZ, []),

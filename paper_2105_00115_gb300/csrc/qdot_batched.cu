@@ -303,6 +303,29 @@ cudaError_t launch_batched_lb(const double* const* xs, const double* const* ys, 
 }
 
 }  // namespace
+
+size_t batched_ws_bytes(const int64_t* ns_host, int count, const qdot_params* p) {
+  long long blocks = 0;
+  for (int i = 0; i < count; ++i) blocks += (ns_host[i] + p->block - 1) / p->block;
+  return batch_layout(count).fixed + align_up(sizeof(chunk::BlockRec) * (size_t)blocks, 256);
+}
+
+cudaError_t launch_qdot_batched(const double* const* xs, const double* const* ys, const long long* ns, int count,
+                                const qdot_params* p, qdot_result* outs, int grid_ctas, void* ws, size_t ws_bytes,
+                                cudaStream_t st) {
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const int grid = grid_ctas > 0 ? grid_ctas : 3 * sms;
+  int lb = 0;
+  while ((1 << lb) < p->block) ++lb;
+  char* w = static_cast<char*>(ws);
+  switch (lb) {
+    case 5: return launch_batched_lb<5>(xs, ys, ns, count, p, outs, grid, w, ws_bytes, st);
+    case 6: return launch_batched_lb<6>(xs, ys, ns, count, p, outs, grid, w, ws_bytes, st);
+    case 7: return launch_batched_lb<7>(xs, ys, ns, count, p, outs, grid, w, ws_bytes, st);
+    default: return launch_batched_lb<8>(xs, ys, ns, count, p, outs, grid, w, ws_bytes, st);
+  }
+}
+
 }  // namespace qd
 
 using namespace qd;
@@ -313,12 +336,9 @@ size_t qdot_batched_workspace_size(const int64_t* ns_host, int32_t count, const 
   std::string why;
   if (count < 0 || !p || !valid_params(0, p, &why) || p->block < 32 || p->block > 256) return 0;
   if (count > 0 && !ns_host) return 0;
-  long long blocks = 0;
-  for (int i = 0; i < count; ++i) {
+  for (int i = 0; i < count; ++i)
     if (ns_host[i] < 0) return 0;
-    blocks += (ns_host[i] + p->block - 1) / p->block;
-  }
-  return batch_layout(count).fixed + align_up(sizeof(chunk::BlockRec) * (size_t)blocks, 256);
+  return batched_ws_bytes(ns_host, count, p);
 }
 
 qdot_status qdot_batched(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
@@ -348,20 +368,9 @@ qdot_status qdot_batched(const double* const* xs, const double* const* ys, const
     set_error("qdot_batched: workspace missing, misaligned or smaller than qdot_batched_workspace_size()");
     return QDOT_ERR_WORKSPACE;
   }
-  const int sms = device_info().sms > 0 ? device_info().sms : 152;
-  const int grid = grid_ctas > 0 ? grid_ctas : 3 * sms;
-  int lb = 0;
-  while ((1 << lb) < p->block) ++lb;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  char* w = static_cast<char*>(ws);
   const long long* nsl = reinterpret_cast<const long long*>(ns);
-  cudaError_t e;
-  switch (lb) {
-    case 5: e = launch_batched_lb<5>(xs, ys, nsl, count, p, outs, grid, w, ws_bytes, st); break;
-    case 6: e = launch_batched_lb<6>(xs, ys, nsl, count, p, outs, grid, w, ws_bytes, st); break;
-    case 7: e = launch_batched_lb<7>(xs, ys, nsl, count, p, outs, grid, w, ws_bytes, st); break;
-    default: e = launch_batched_lb<8>(xs, ys, nsl, count, p, outs, grid, w, ws_bytes, st); break;
-  }
+  const cudaError_t e = launch_qdot_batched(xs, ys, nsl, count, p, outs, grid_ctas, ws, ws_bytes, st);
   if (e != cudaSuccess) {
     set_error(std::string("qdot_batched launch: ") + cudaGetErrorString(e));
     return QDOT_ERR_CUDA;

@@ -143,9 +143,9 @@ __device__ __forceinline__ void load_item(const double* __restrict__ x, const do
 // out [stage][array][j][lane], and later reads back exactly those pieces, so
 // no lane ever reads what another lane wrote.
 // ---------------------------------------------------------------------------
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr int kStageWords = 2 * 4 * 32;              // uint4 per stage
-constexpr int kRingBytes = kStages * kStageWords * 16;  // per warp: 12 KB
+constexpr int kRingBytes = kStages * kStageWords * 16;  // per warp: 8 KB
 
 __device__ __forceinline__ void cp_async16(uint4* dst, const void* src, int src_bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(dst);

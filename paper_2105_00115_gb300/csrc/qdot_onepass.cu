@@ -38,7 +38,7 @@ using namespace chunk;
 
 constexpr int kOpThreads = 256;
 constexpr int kOpWarps = kOpThreads / 32;
-constexpr int kOpCtasPerSm = 2;                       // 2 x 96 KB of staging per SM
+constexpr int kOpCtasPerSm = 3;                       // 3 x 64 KB of staging per SM
 constexpr int kOpSmem = kOpWarps * kRingBytes;
 
 // Per-warp record written to the workspace.

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "qdot_common.cuh"
 #include "qdot_internal.h"
@@ -243,12 +244,12 @@ cudaError_t record_graph(Body body, int iters, cudaGraphExec_t* exec) {
 }
 
 // Replay the graph until the device flag says done (checked once per replay).
-cudaError_t run_until_done(cudaGraphExec_t exec, const SolverState* st, int max_replays, cudaStream_t stream) {
+cudaError_t run_until_done(cudaGraphExec_t exec, const int* done_flag, int max_replays, cudaStream_t stream) {
   for (int r = 0; r < max_replays; ++r) {
     cudaError_t e = cudaGraphLaunch(exec, stream);
     if (e != cudaSuccess) return e;
     int done = 0;
-    e = cudaMemcpyAsync(&done, &st->done, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    e = cudaMemcpyAsync(&done, done_flag, sizeof(int), cudaMemcpyDeviceToHost, stream);
     if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return e;
@@ -294,6 +295,268 @@ qdot_status check_csr(const qdot_csr* A, const char* who) {
 qdot_status fail(const char* who, cudaError_t e) {
   set_error(std::string(who) + ": " + cudaGetErrorString(e));
   return QDOT_ERR_CUDA;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched ACG: `count` independent SPD systems (the diagonal blocks of one
+// block-diagonal CSR matrix) solved together, every kernel of an iteration
+// covering all systems: one SpMV launch, one batched qdot launch per dot
+// product, one launch per vector update.  Each system keeps its own scalars
+// and stops on its own; a stopped system's rows are skipped and its dot
+// products get length 0.  Internal vectors use padded offsets so that every
+// system's slice starts on a 16-byte boundary (the batched qdot needs it).
+// Work over rows is split into tiles of 256 rows of one system.
+// ---------------------------------------------------------------------------
+constexpr int kTileRows = 256;
+
+struct BatchSys {
+  double c, bnorm;
+  double alpha, beta;
+  int k, active, status, pad;
+  long long counts[5];
+};
+
+struct RowTile {
+  int sys, nrows;
+  long long row0;  // first row (global, unpadded)
+};
+
+struct BatchView {
+  const long long* off;   // [count + 1] row offsets of the systems
+  const long long* poff;  // [count + 1] padded offsets of their internal slices
+  const RowTile* tiles;
+  long long ntiles;
+  int count;
+};
+
+__device__ __forceinline__ long long padded(const BatchView& v, int s, long long r) {
+  return r - v.off[s] + v.poff[s];
+}
+
+// dst_pad = A src (src padded, or the caller's unpadded x), rows of active
+// systems only when `sys` is given.  A column outside its row's system is
+// skipped and flags *bad.
+__global__ void k_bcg_spmv(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, BatchView v, const double* __restrict__ src,
+                           int src_padded, double* __restrict__ dst, const BatchSys* __restrict__ sys,
+                           int* __restrict__ bad) {
+  for (long long t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+    const RowTile tile = v.tiles[t];
+    if (sys && !sys[tile.sys].active) continue;
+    if ((int)threadIdx.x >= tile.nrows) continue;
+    const int s = tile.sys;
+    const long long r = tile.row0 + threadIdx.x;
+    const long long lo = v.off[s], hi = v.off[s + 1], shift = v.poff[s] - lo;
+    double acc = 0.0;
+    for (long long k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+      const long long c = col[k];
+      if (c < lo || c >= hi) {
+        *bad = 1;
+        continue;
+      }
+      acc = fma(val[k], __ldg(src + (src_padded ? c + shift : c)), acc);
+    }
+    dst[r + shift] = acc;
+  }
+}
+
+__global__ void k_bcg_init_vectors(BatchView v, const double* __restrict__ b, const double* __restrict__ ax,
+                                   double* __restrict__ r, double* __restrict__ p, double* __restrict__ bp) {
+  for (long long t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+    const RowTile tile = v.tiles[t];
+    if ((int)threadIdx.x >= tile.nrows) continue;
+    const long long row = tile.row0 + threadIdx.x;
+    const long long i = padded(v, tile.sys, row);
+    const double d = b[row] - ax[i];
+    r[i] = d;
+    p[i] = d;
+    bp[i] = b[row];
+  }
+}
+
+__global__ void k_bcg_init_state(BatchSys* __restrict__ sys, const qdot_result* __restrict__ rr,
+                                 const qdot_result* __restrict__ bb, long long* __restrict__ ns_dot, int count,
+                                 double tol, int max_it, int* __restrict__ remaining) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;  // *remaining and *all_done start at 0
+  if (s >= count) return;
+  BatchSys st = {};
+  st.c = rr[s].value;
+  st.bnorm = sqrt(bb[s].value);
+  st.status = rr[s].status != QDOT_OK ? rr[s].status : bb[s].status;
+  for (int k = 0; k < 5; ++k) st.counts[k] = rr[s].count[k];
+  st.active = st.status == QDOT_OK && 0 < max_it && sqrt(st.c) / st.bnorm > tol;
+  sys[s] = st;
+  if (!st.active) ns_dot[s] = 0;
+  if (st.active) atomicAdd(remaining, 1);
+}
+
+__global__ void k_bcg_all_done(const int* __restrict__ remaining, int* __restrict__ all_done) {
+  *all_done = *remaining == 0;
+}
+
+__global__ void k_bcg_alpha(BatchSys* __restrict__ sys, const qdot_result* __restrict__ pq, int count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= count || !sys[s].active) return;
+  for (int k = 0; k < 5; ++k) sys[s].counts[k] += pq[s].count[k];
+  if (pq[s].status != QDOT_OK) sys[s].status = pq[s].status;
+  sys[s].alpha = sys[s].c / pq[s].value;
+}
+
+__global__ void k_bcg_update(BatchView v, double* __restrict__ x, double* __restrict__ r,
+                             const double* __restrict__ p, const double* __restrict__ q,
+                             const BatchSys* __restrict__ sys) {
+  for (long long t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+    const RowTile tile = v.tiles[t];
+    const BatchSys& st = sys[tile.sys];
+    if (!st.active || (int)threadIdx.x >= tile.nrows) continue;
+    const long long row = tile.row0 + threadIdx.x;
+    const long long i = padded(v, tile.sys, row);
+    const double a = st.alpha;
+    x[row] = fma(a, p[i], x[row]);
+    r[i] = fma(-a, q[i], r[i]);
+  }
+}
+
+__global__ void k_bcg_beta(BatchSys* __restrict__ sys, const qdot_result* __restrict__ rr, int count, double tol,
+                           int max_it, long long* __restrict__ ns_dot, int* __restrict__ remaining) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < count && sys[s].active) {
+    BatchSys& st = sys[s];
+    for (int k = 0; k < 5; ++k) st.counts[k] += rr[s].count[k];
+    if (rr[s].status != QDOT_OK) st.status = rr[s].status;
+    const double c_new = rr[s].value;
+    st.beta = c_new / st.c;
+    st.c = c_new;
+    st.k += 1;
+    if (st.status != QDOT_OK || !(st.k < max_it && sqrt(st.c) / st.bnorm > tol)) {
+      st.active = 0;  // p is still updated once below; nothing reads it afterwards
+      ns_dot[s] = 0;
+      atomicSub(remaining, 1);
+    }
+  }
+}
+
+__global__ void k_bcg_p(BatchView v, double* __restrict__ p, const double* __restrict__ r,
+                        const BatchSys* __restrict__ sys) {
+  for (long long t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+    const RowTile tile = v.tiles[t];
+    const BatchSys& st = sys[tile.sys];
+    if (!st.active || (int)threadIdx.x >= tile.nrows) continue;
+    const long long i = padded(v, tile.sys, tile.row0 + threadIdx.x);
+    p[i] = fma(st.beta, p[i], r[i]);
+  }
+}
+
+__global__ void k_bcg_residual(BatchView v, const double* __restrict__ bp, const double* __restrict__ ax,
+                               double* __restrict__ res) {
+  for (long long t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+    const RowTile tile = v.tiles[t];
+    if ((int)threadIdx.x >= tile.nrows) continue;
+    const long long i = padded(v, tile.sys, tile.row0 + threadIdx.x);
+    res[i] = bp[i] - ax[i];
+  }
+}
+
+__global__ void k_bcg_finish(const BatchSys* __restrict__ sys, const qdot_result* __restrict__ true_rr, int count,
+                             double tol, const int* __restrict__ bad, qdot_cg_info* __restrict__ infos) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= count) return;
+  const BatchSys st = sys[s];
+  qdot_cg_info o;
+  o.iters = st.k;
+  o.relres = sqrt(st.c) / st.bnorm;
+  o.status = *bad ? QDOT_ERR_ARG
+                  : (st.status != QDOT_OK ? st.status : (o.relres > tol ? QDOT_ERR_NOCONV : QDOT_OK));
+  o.true_relres = sqrt(true_rr[s].value) / st.bnorm;
+  for (int k = 0; k < 5; ++k) o.counts[k] = st.counts[k];
+  infos[s] = o;
+}
+
+// Plain FP64 dot per system (the comparator): per-tile partial sums, then one
+// warp per system adds its tiles in order (deterministic).
+__global__ void k_bcg_dot_tiles(BatchView v, const double* __restrict__ a, const double* __restrict__ b,
+                                double* __restrict__ part, const long long* __restrict__ ns_dot) {
+  __shared__ double sw[kTileRows / 32];
+  for (long long t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+    const RowTile tile = v.tiles[t];
+    double acc = 0.0;
+    if (ns_dot[tile.sys] > 0 && (int)threadIdx.x < tile.nrows) {
+      const long long i = padded(v, tile.sys, tile.row0 + threadIdx.x);
+      acc = a[i] * b[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < kTileRows / 32; ++w) sum += sw[w];
+      part[t] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_bcg_dot_final(const double* __restrict__ part, const long long* __restrict__ tile_start, int count,
+                                qdot_result* __restrict__ out) {
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= count) return;
+  double acc = 0.0;
+  for (long long t = tile_start[s] + lane; t < tile_start[s + 1]; t += 32) acc += part[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    qdot_result r = {};
+    r.value = acc;
+    r.status = QDOT_OK;
+    out[s] = r;
+  }
+}
+
+struct BatchLayoutCg {
+  size_t off_sys, off_res, off_nsd, off_nsf, off_off, off_poff, off_tiles, off_tstart, off_part, off_ptr, off_flags,
+      off_vec, off_qws, total;
+  long long ntiles, total_pad;
+  size_t qws_bytes;
+};
+
+BatchLayoutCg batch_cg_layout(const int64_t* row_off, int count, const qdot_params* qp) {
+  BatchLayoutCg l;
+  long long ntiles = 0, pad = 0;
+  std::vector<int64_t> ns(count);
+  for (int s = 0; s < count; ++s) {
+    const long long m = row_off[s + 1] - row_off[s];
+    ns[s] = m;
+    ntiles += (m + kTileRows - 1) / kTileRows;
+    pad += (m + 1) & ~1ll;  // slices of an even number of doubles: 16-byte aligned starts
+  }
+  l.ntiles = ntiles;
+  l.total_pad = pad;
+  const qdot_params exact = {1e-300, 32, 1, 0, QDOT_PATH_AUTO};
+  l.qws_bytes = std::max(batched_ws_bytes(ns.data(), count, qp), batched_ws_bytes(ns.data(), count, &exact));
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  l.off_sys = take(sizeof(BatchSys) * count);
+  l.off_res = take(sizeof(qdot_result) * 3 * count);
+  l.off_nsd = take(sizeof(long long) * count);
+  l.off_nsf = take(sizeof(long long) * count);
+  l.off_off = take(sizeof(long long) * (count + 1));
+  l.off_poff = take(sizeof(long long) * (count + 1));
+  l.off_tiles = take(sizeof(RowTile) * (ntiles > 0 ? ntiles : 1));
+  l.off_tstart = take(sizeof(long long) * (count + 1));
+  l.off_part = take(sizeof(double) * (ntiles > 0 ? ntiles : 1));
+  l.off_ptr = take(sizeof(double*) * 4 * count);
+  l.off_flags = take(sizeof(int) * 4);
+  l.off_vec = take(sizeof(double) * 4 * (size_t)pad);
+  l.off_qws = take(l.qws_bytes);
+  l.total = off;
+  return l;
 }
 
 }  // namespace
@@ -363,7 +626,7 @@ qdot_status qdot_cg(const qdot_csr* A, const double* b, double* x, double rel_to
   };
   cudaGraphExec_t exec = nullptr;
   if ((e = record_graph(body, kIterPerGraph, &exec)) != cudaSuccess) return fail("qdot_cg: graph", e);
-  e = run_until_done(exec, st, max_it / kIterPerGraph + 2, s);
+  e = run_until_done(exec, &st->done, max_it / kIterPerGraph + 2, s);
   cudaGraphExecDestroy(exec);
   if (e != cudaSuccess) return fail("qdot_cg", e);
   // true residual ||b - A x|| / ||b|| (exact dot)
@@ -424,11 +687,174 @@ qdot_status qdot_power(const qdot_csr* A, double* x, int32_t iters, double tau, 
   };
   cudaGraphExec_t exec = nullptr;
   if ((e = record_graph(body, kIterPerGraph, &exec)) != cudaSuccess) return fail("qdot_power: graph", e);
-  e = run_until_done(exec, st, iters / kIterPerGraph + 2, s);
+  e = run_until_done(exec, &st->done, iters / kIterPerGraph + 2, s);
   cudaGraphExecDestroy(exec);
   if (e != cudaSuccess) return fail("qdot_power", e);
   k_pm_finish<<<1, 1, 0, s>>>(st, info);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail("qdot_power", e);
+  return QDOT_OK;
+}
+
+
+size_t qdot_cg_batched_workspace_size(const int64_t* row_off_host, int32_t count, const qdot_params* p) {
+  if (!row_off_host || count <= 0 || !p) return 0;
+  for (int s = 0; s < count; ++s)
+    if (row_off_host[s + 1] < row_off_host[s] || row_off_host[0] != 0) return 0;
+  qdot_params qp = *p;
+  if (qp.path == QDOT_PATH_FP64_DOT) qp = qdot_params{1e-16, 32, 1, 0, QDOT_PATH_AUTO};
+  std::string why;
+  if (!valid_params(0, &qp, &why) || qp.block < 32 || qp.block > 256) return 0;
+  return batch_cg_layout(row_off_host, count, &qp).total;
+}
+
+qdot_status qdot_cg_batched(const qdot_csr* A, const int64_t* row_off_host, int32_t count, const double* b,
+                            double* x, double rel_tol, int32_t max_it, const qdot_params* p, qdot_cg_info* infos,
+                            void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!p) {
+    set_error("qdot_cg_batched: params pointer is NULL");
+    return QDOT_ERR_ARG;
+  }
+  const bool plain = p->path == QDOT_PATH_FP64_DOT;
+  qdot_params qp = plain ? qdot_params{1e-16, 32, 1, 0, QDOT_PATH_AUTO} : *p;
+  std::string why;
+  if (!valid_params(0, &qp, &why) || qp.block < 32 || qp.block > 256) {
+    set_error("qdot_cg_batched: " + (why.empty() ? std::string("block must be a power of two in [32, 256]") : why));
+    return QDOT_ERR_ARG;
+  }
+  if (check_csr(A, "qdot_cg_batched") != QDOT_OK) return QDOT_ERR_ARG;
+  if (!row_off_host || count <= 0 || row_off_host[0] != 0 || row_off_host[count] != A->n || !b || !x || !infos ||
+      max_it < 0 || !(rel_tol >= 0.0)) {
+    set_error("qdot_cg_batched: need count > 0 host row offsets from 0 to A->n, device b, x, infos, max_it >= 0 "
+              "and rel_tol >= 0");
+    return QDOT_ERR_ARG;
+  }
+  for (int s = 0; s < count; ++s)
+    if (row_off_host[s + 1] < row_off_host[s]) {
+      set_error("qdot_cg_batched: row offsets must not decrease");
+      return QDOT_ERR_ARG;
+    }
+  const BatchLayoutCg l = batch_cg_layout(row_off_host, count, &qp);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < l.total) {
+    set_error("qdot_cg_batched: workspace missing, misaligned or smaller than qdot_cg_batched_workspace_size()");
+    return QDOT_ERR_WORKSPACE;
+  }
+  char* w = static_cast<char*>(ws);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto* sys = reinterpret_cast<BatchSys*>(w + l.off_sys);
+  auto* res = reinterpret_cast<qdot_result*>(w + l.off_res);  // [0, count) p.q, [count, 2 count) r.r, then b.b
+  qdot_result* res_pq = res;
+  qdot_result* res_rr = res + count;
+  qdot_result* res_bb = res + 2 * count;
+  auto* ns_dot = reinterpret_cast<long long*>(w + l.off_nsd);
+  auto* ns_full = reinterpret_cast<long long*>(w + l.off_nsf);
+  auto* d_off = reinterpret_cast<long long*>(w + l.off_off);
+  auto* d_poff = reinterpret_cast<long long*>(w + l.off_poff);
+  auto* d_tiles = reinterpret_cast<RowTile*>(w + l.off_tiles);
+  auto* d_tstart = reinterpret_cast<long long*>(w + l.off_tstart);
+  auto* d_part = reinterpret_cast<double*>(w + l.off_part);
+  auto* d_ptr = reinterpret_cast<const double**>(w + l.off_ptr);  // p, q, r, b-copy slices
+  auto* flags = reinterpret_cast<int*>(w + l.off_flags);            // remaining, all_done, bad
+  double* r = reinterpret_cast<double*>(w + l.off_vec);
+  double* pv = r + l.total_pad;
+  double* q = pv + l.total_pad;
+  double* bp = q + l.total_pad;
+  void* qws = w + l.off_qws;
+  // host-built tables, copied once
+  std::vector<long long> h_off(count + 1), h_poff(count + 1), h_tstart(count + 1), h_ns(count);
+  std::vector<RowTile> h_tiles;
+  h_tiles.reserve((size_t)l.ntiles);
+  std::vector<const double*> h_ptr(4 * (size_t)count);
+  long long pad = 0;
+  for (int s = 0; s < count; ++s) {
+    const long long m = row_off_host[s + 1] - row_off_host[s];
+    h_off[s] = row_off_host[s];
+    h_poff[s] = pad;
+    h_ns[s] = m;
+    h_tstart[s] = (long long)h_tiles.size();
+    for (long long t0 = 0; t0 < m; t0 += kTileRows)
+      h_tiles.push_back(RowTile{s, (int)std::min<long long>(kTileRows, m - t0), row_off_host[s] + t0});
+    h_ptr[s] = pv + pad;
+    h_ptr[count + s] = q + pad;
+    h_ptr[2 * count + s] = r + pad;
+    h_ptr[3 * count + s] = bp + pad;
+    pad += (m + 1) & ~1ll;
+  }
+  h_off[count] = row_off_host[count];
+  h_poff[count] = pad;
+  h_tstart[count] = (long long)h_tiles.size();
+  cudaError_t e;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  if ((e = up(d_off, h_off.data(), sizeof(long long) * (count + 1))) != cudaSuccess ||
+      (e = up(d_poff, h_poff.data(), sizeof(long long) * (count + 1))) != cudaSuccess ||
+      (e = up(d_tstart, h_tstart.data(), sizeof(long long) * (count + 1))) != cudaSuccess ||
+      (e = up(d_tiles, h_tiles.data(), sizeof(RowTile) * h_tiles.size())) != cudaSuccess ||
+      (e = up(d_ptr, h_ptr.data(), sizeof(double*) * h_ptr.size())) != cudaSuccess ||
+      (e = up(ns_dot, h_ns.data(), sizeof(long long) * count)) != cudaSuccess ||
+      (e = up(ns_full, h_ns.data(), sizeof(long long) * count)) != cudaSuccess ||
+      (e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(res, 0, 3 * sizeof(qdot_result) * count, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(r, 0, 4 * sizeof(double) * (size_t)l.total_pad, st)) != cudaSuccess)
+    return fail("qdot_cg_batched: setup", e);
+  // the host tables must outlive the copies
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail("qdot_cg_batched: setup", e);
+
+  const BatchView v = {d_off, d_poff, d_tiles, l.ntiles, count};
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const int tgrid = (int)std::max<long long>(1, std::min<long long>(l.ntiles, (long long)sms * 8));
+  const int sgrid = (count + 255) / 256;
+  const long long* rowptr = reinterpret_cast<const long long*>(A->rowptr);
+  const qdot_params exact = {1e-300, 32, 1, 0, QDOT_PATH_AUTO};
+  const double* const* P = d_ptr;
+  const double* const* Q = d_ptr + count;
+  const double* const* R = d_ptr + 2 * count;
+  const double* const* BP = d_ptr + 3 * count;
+  auto dots = [&](const double* const* xs, const double* const* ys, const double* xa, const double* ya,
+                  const long long* ns, const qdot_params* prm, bool use_plain, qdot_result* out,
+                  cudaStream_t cs) -> cudaError_t {
+    if (use_plain) {
+      k_bcg_dot_tiles<<<tgrid, kTileRows, 0, cs>>>(v, xa, ya, d_part, ns);
+      k_bcg_dot_final<<<(count + 7) / 8, 256, 0, cs>>>(d_part, d_tstart, count, out);
+      return cudaGetLastError();
+    }
+    return launch_qdot_batched(xs, ys, ns, count, prm, out, 0, qws, l.qws_bytes, cs);
+  };
+  // r0 = b - A x0, p0 = r0, c0 = r0.r0, ||b|| (double class)
+  k_bcg_spmv<<<tgrid, kTileRows, 0, st>>>(rowptr, A->col, A->val, v, x, 0, q, nullptr, flags + 2);
+  k_bcg_init_vectors<<<tgrid, kTileRows, 0, st>>>(v, b, q, r, pv, bp);
+  if ((e = dots(R, R, r, r, ns_dot, &qp, plain, res_rr, st)) != cudaSuccess) return fail("qdot_cg_batched", e);
+  if ((e = dots(BP, BP, bp, bp, ns_full, &exact, false, res_bb, st)) != cudaSuccess)
+    return fail("qdot_cg_batched", e);
+  k_bcg_init_state<<<sgrid, 256, 0, st>>>(sys, res_rr, res_bb, ns_dot, count, rel_tol, max_it, flags);
+  k_bcg_all_done<<<1, 1, 0, st>>>(flags, flags + 1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail("qdot_cg_batched", e);
+  auto body = [&](cudaStream_t cs) -> cudaError_t {
+    k_bcg_spmv<<<tgrid, kTileRows, 0, cs>>>(rowptr, A->col, A->val, v, pv, 1, q, sys, flags + 2);
+    cudaError_t ee = dots(P, Q, pv, q, ns_dot, &qp, plain, res_pq, cs);
+    if (ee != cudaSuccess) return ee;
+    k_bcg_alpha<<<sgrid, 256, 0, cs>>>(sys, res_pq, count);
+    k_bcg_update<<<tgrid, kTileRows, 0, cs>>>(v, x, r, pv, q, sys);
+    ee = dots(R, R, r, r, ns_dot, &qp, plain, res_rr, cs);
+    if (ee != cudaSuccess) return ee;
+    k_bcg_beta<<<sgrid, 256, 0, cs>>>(sys, res_rr, count, rel_tol, max_it, ns_dot, flags);
+    k_bcg_p<<<tgrid, kTileRows, 0, cs>>>(v, pv, r, sys);
+    k_bcg_all_done<<<1, 1, 0, cs>>>(flags, flags + 1);
+    return cudaGetLastError();
+  };
+  cudaGraphExec_t exec = nullptr;
+  if ((e = record_graph(body, kIterPerGraph, &exec)) != cudaSuccess) return fail("qdot_cg_batched: graph", e);
+  e = run_until_done(exec, flags + 1, max_it / kIterPerGraph + 2, st);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return fail("qdot_cg_batched", e);
+  // true residuals ||b - A x|| / ||b|| (double class)
+  k_bcg_spmv<<<tgrid, kTileRows, 0, st>>>(rowptr, A->col, A->val, v, x, 0, q, nullptr, flags + 2);
+  k_bcg_residual<<<tgrid, kTileRows, 0, st>>>(v, bp, q, r);
+  if ((e = dots(R, R, r, r, ns_full, &exact, false, res_pq, st)) != cudaSuccess) return fail("qdot_cg_batched", e);
+  k_bcg_finish<<<sgrid, 256, 0, st>>>(sys, res_pq, count, rel_tol, flags + 2, infos);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail("qdot_cg_batched", e);
   return QDOT_OK;
 }
 

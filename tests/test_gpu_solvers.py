@@ -132,3 +132,63 @@ def test_power_iters_zero(q):
     lam, x, info, _ = q.power(q.Csr(rp, col, val), _dev(x0), iters=0)
     assert info["iters"] == 0 and lam == 0.0
     np.testing.assert_array_equal(x.cpu().numpy(), x0)
+
+
+def _systems(kind, edges, seed=500):
+    blocks = []
+    for i, e in enumerate(edges):
+        if kind == "laplace":
+            blocks.append(workloads.laplace3d(e, e + 1, e))
+        else:
+            blocks.append(workloads.poisson3d(e, e, e, seed=seed + i))
+    return blocks
+
+
+@pytest.mark.parametrize("block,eps", [(32, 1e-16), (32, 1e-6), (64, 1e-3), (256, 1e-8)])
+def test_cg_batched_matches_single(q, orc, block, eps):
+    """Each system of the batch follows the single-system solver exactly (the
+    batched qdot and the single qdot compute the same values) and, on these
+    well-conditioned operators, takes the oracle's iteration count."""
+    blocks = _systems("laplace", [3, 6, 4, 9, 5, 7, 8])
+    rp, col, val, off = workloads.block_diagonal(blocks)
+    b = workloads.rhs(int(off[-1]), seed=77)
+    x, infos = q.cg_batched(q.Csr(rp, col, val), off, _dev(b), rel_tol=1e-10, max_it=3000, eps=eps, block=block)
+    xg = x.cpu().numpy()
+    for s, (brp, bcol, bval) in enumerate(blocks):
+        bs = b[off[s]:off[s + 1]]
+        xs1, info1, _ = q.cg(q.Csr(brp, bcol, bval), _dev(bs), rel_tol=1e-10, max_it=3000, eps=eps, block=block)
+        assert infos[s]["status"] == 0 and infos[s]["iters"] == info1["iters"], (s, infos[s], info1)
+        np.testing.assert_allclose(xg[off[s]:off[s + 1]], xs1.cpu().numpy(), rtol=0, atol=1e-12 * np.abs(xg).max())
+        xo, it, rr, counts, st = orc.cg(brp, bcol, bval, bs, rel_tol=1e-10, max_it=3000, eps=eps, block=block)
+        assert it == infos[s]["iters"]
+        assert infos[s]["relres"] <= 1e-10 and infos[s]["true_relres"] <= 1e-9
+
+
+def test_cg_batched_variable_coefficients_and_fp64(q, orc):
+    blocks = _systems("poisson", [4, 7, 5, 6])
+    rp, col, val, off = workloads.block_diagonal(blocks)
+    b = workloads.rhs(int(off[-1]), seed=78)
+    A = q.Csr(rp, col, val)
+    x, infos = q.cg_batched(A, off, _dev(b), rel_tol=1e-10, max_it=20000, eps=1e-8, block=32)
+    x64, i64 = q.cg_batched(A, off, _dev(b), rel_tol=1e-10, max_it=20000, dot="fp64")
+    for s, (brp, bcol, bval) in enumerate(blocks):
+        bs = b[off[s]:off[s + 1]]
+        xo, it, rr, counts, st = orc.cg(brp, bcol, bval, bs, rel_tol=1e-10, max_it=20000, eps=1e-8, block=32)
+        assert infos[s]["status"] == 0 and infos[s]["relres"] <= 1e-10
+        assert abs(infos[s]["iters"] - it) <= max(3, 0.03 * it)
+        # plain FP64 dots: converges (on these tiny ill-conditioned systems the
+        # count itself moves with the summation order of the dots)
+        assert i64[s]["status"] == 0 and sum(i64[s]["counts"]) == 0 and i64[s]["relres"] <= 1e-10
+
+
+def test_cg_batched_iteration_cap_and_bad_column(q):
+    blocks = _systems("laplace", [5, 6])
+    rp, col, val, off = workloads.block_diagonal(blocks)
+    b = workloads.rhs(int(off[-1]), seed=79)
+    x, infos = q.cg_batched(q.Csr(rp, col, val), off, _dev(b), rel_tol=1e-14, max_it=5, eps=1e-16, block=32)
+    assert all(i["iters"] == 5 and i["status"] == q.QDOT_ERR_NOCONV for i in infos)
+    # a column that reaches into the other system is refused (not read)
+    col2 = col.copy()
+    col2[3] = int(off[1]) + 2
+    x, infos = q.cg_batched(q.Csr(rp, col2, val), off, _dev(b), rel_tol=1e-10, max_it=50, eps=1e-16, block=32)
+    assert all(i["status"] == q.QDOT_ERR_ARG for i in infos)

@@ -165,3 +165,28 @@ def rhs(n: int, seed: int = 2110) -> np.ndarray:
 def unit_start(n: int, seed: int = 2111) -> np.ndarray:
     v = np.random.default_rng(seed).uniform(-1.0, 1.0, n)
     return v / np.sqrt(np.dot(v, v))
+
+
+def block_diagonal(blocks):
+    """One CSR matrix with the given (rowptr, col, val) blocks on its diagonal;
+    returns (rowptr, col, val, row_off)."""
+    rps, cols, vals, offs = [np.zeros(1, dtype=np.int64)], [], [], [0]
+    nnz = 0
+    for rp, col, val in blocks:
+        n = rp.shape[0] - 1
+        rps.append(rp[1:] + nnz)
+        cols.append(col.astype(np.int64) + offs[-1])
+        vals.append(val)
+        nnz += int(rp[-1])
+        offs.append(offs[-1] + n)
+    return (np.concatenate(rps), np.concatenate(cols).astype(np.int32), np.concatenate(vals),
+            np.array(offs, dtype=np.int64))
+
+
+def batched_cg_systems(count: int = 256, lo: int = 16, hi: int = 64, seed: int = 2112):
+    """`count` variable-coefficient 7-point systems on cubic grids with edges
+    uniform in [lo, hi], block-diagonal; returns (rowptr, col, val, row_off, edges)."""
+    rng = np.random.default_rng(seed)
+    edges = rng.integers(lo, hi + 1, count)
+    blocks = [poisson3d(int(e), int(e), int(e), seed=seed + 1 + i) for i, e in enumerate(edges)]
+    return (*block_diagonal(blocks), edges)
