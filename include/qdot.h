@@ -170,13 +170,32 @@ qdot_status qdot_explain(const double* x, const double* y, int64_t n, const qdot
  *            or the problem's status is QDOT_ERR_ARG).
  *   ns       device array of `count` lengths (int64, >= 0).
  *   outs     device array of `count` qdot_result.
- *   grid_ctas  CTAs of the streaming kernel (0 = two per SM); a tuning knob.
+ *   grid_ctas  CTAs of the streaming kernel (0 = three per SM); see also
+ *            qdot_batched_tuned().
  *   ws       workspace of qdot_batched_workspace_size(ns_host, count, p)
  *            bytes, computed from the same lengths on the host; if it is too
  *            small every problem reports QDOT_ERR_WORKSPACE.
  * Nothing synchronises with the host, so the call can be recorded in a CUDA
  * graph and replayed. */
 size_t qdot_batched_workspace_size(const int64_t* ns_host, int32_t count, const qdot_params* p);
+
+/* Launch shape of the batched streaming kernel (the one persistent launch).
+ * Every lane always handles 8 components of a warp item of 256 (the
+ * block-to-lane mapping needs it); the tunable parts are the CTA size, how
+ * many CTAs (and so how many warps split the concatenated items of all pairs)
+ * and whether items are staged through shared memory. */
+typedef struct {
+  int32_t threads_per_cta;  /* 128 or 256 */
+  int32_t ctas_per_sm;      /* grid = ctas_per_sm * SMs when grid_ctas == 0; 1..64 */
+  int32_t grid_ctas;        /* explicit grid size, or 0 */
+  int32_t staged;           /* 1: cp.async staging through shared memory; 0: register double buffering */
+} qdot_batched_tuning;
+
+/* qdot_batched() with an explicit launch shape (tuning == NULL: 256 threads,
+ * 3 CTAs per SM, staged); grid_ctas > 0 overrides the tuning's grid. */
+qdot_status qdot_batched_tuned(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
+                               const qdot_params* p, qdot_result* outs, const qdot_batched_tuning* tuning,
+                               int32_t grid_ctas, void* ws, size_t ws_bytes, void* stream);
 qdot_status qdot_batched(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
                          const qdot_params* p, qdot_result* outs, int32_t grid_ctas, void* ws, size_t ws_bytes,
                          void* stream);

@@ -209,13 +209,20 @@ class Batch:
             raise QdotError(1, "invalid batched qdot parameters (block must be a power of two in [32, 256])")
         self.ws = _workspace(need, dev)
         self.outs = torch.empty(max(self.count, 1) * ctypes.sizeof(Result), dtype=torch.uint8, device=dev)
+        self.tuning = None  # an _abi.BatchedTuning, set by autotune()
 
     def launch(self, stream=None):
         lib = load()
-        st = lib.qdot_batched(_ptr(self.xs_dev), _ptr(self.ys_dev), _ptr(self.ns_dev), self.count,
-                              ctypes.byref(self.p), _ptr(self.outs), self.grid_ctas, _ptr(self.ws), self.ws.numel(),
-                              _stream_ptr(stream))
+        st = lib.qdot_batched_tuned(_ptr(self.xs_dev), _ptr(self.ys_dev), _ptr(self.ns_dev), self.count,
+                                    ctypes.byref(self.p), _ptr(self.outs),
+                                    ctypes.byref(self.tuning) if self.tuning is not None else None, self.grid_ctas,
+                                    _ptr(self.ws), self.ws.numel(), _stream_ptr(stream))
         check(st, lib)
+
+    def autotune(self, reps=5, use_cache=True, path=None):
+        """Time every launch shape on this batch and keep the fastest (cached)."""
+        from .tune import tune_batched
+        return tune_batched(self, reps=reps, use_cache=use_cache, path=path)
 
     def results(self):
         return _decode_results(self.outs.cpu().numpy()[: self.count * ctypes.sizeof(Result)], self.count)

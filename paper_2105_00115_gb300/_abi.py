@@ -37,6 +37,11 @@ class Csr(ctypes.Structure):
                 ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
+class BatchedTuning(ctypes.Structure):
+    _fields_ = [("threads_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("staged", ctypes.c_int32)]
+
+
 class CgInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres", ctypes.c_double),
                 ("true_relres", ctypes.c_double), ("counts", ctypes.c_int64 * 5)]
@@ -68,6 +73,7 @@ SIGNATURES = {
     "qdot_backward": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP]),
     "qdot_batched_backward_workspace_size": (_SZ, [_I32]),
     "qdot_batched_backward": (ctypes.c_int, [_VP, _VP, _VP, _I32, _PP, _VP, _VP, _VP, _VP, _I32, _VP, _SZ, _VP]),
+    "qdot_batched_tuned": (ctypes.c_int, [_VP, _VP, _VP, _I32, _PP, _VP, _VP, _I32, _VP, _SZ, _VP]),
     "qdot_cg_workspace_size": (_SZ, [_I64, _PP]),
     "qdot_cg": (ctypes.c_int, [_VP, _VP, _VP, _D, _I32, _PP, _VP, _VP, _VP, _SZ, _VP]),
     "qdot_cg_batched_workspace_size": (_SZ, [_VP, _I32, _PP]),

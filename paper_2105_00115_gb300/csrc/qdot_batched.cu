@@ -112,22 +112,24 @@ __device__ __forceinline__ int find_pair(const long long* __restrict__ gpre, int
   return lo;
 }
 
-template <int LOG2B>
-__global__ void __launch_bounds__(kBThreads, 3) k_bstream(const double* const* __restrict__ xs,
-                                                          const double* const* __restrict__ ys,
-                                                          const long long* __restrict__ ns, int count,
-                                                          const long long* __restrict__ gpre,
-                                                          const long long* __restrict__ bpre,
-                                                          PairStats* __restrict__ ps,
-                                                          const BatchHeader* __restrict__ hdr,
-                                                          BlockRec* __restrict__ recs) {
+// THREADS per CTA; STAGED: items staged through shared memory with cp.async
+// (one item ahead), else double-buffered in registers.
+template <int LOG2B, int THREADS, bool STAGED>
+__global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream(const double* const* __restrict__ xs,
+                                                                  const double* const* __restrict__ ys,
+                                                                  const long long* __restrict__ ns, int count,
+                                                                  const long long* __restrict__ gpre,
+                                                                  const long long* __restrict__ bpre,
+                                                                  PairStats* __restrict__ ps,
+                                                                  const BatchHeader* __restrict__ hdr,
+                                                                  BlockRec* __restrict__ recs) {
   constexpr int L = Map<LOG2B>::L, BPI = Map<LOG2B>::BPI;
   if (hdr->status != QDOT_OK) return;
   const int lane = threadIdx.x & 31;
   const int g = lane / L, sub = lane % L;
   const long long total = hdr->total_groups;  // warp items over all pairs
-  const long long gwarp = ((long long)blockIdx.x * kBThreads + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * kBThreads) >> 5;
+  const long long gwarp = ((long long)blockIdx.x * THREADS + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * THREADS) >> 5;
   const long long per = (total + nwarps - 1) / nwarps;
   const long long g0 = min(total, gwarp * per), g1 = min(total, g0 + per);
   if (g0 >= g1) return;
@@ -154,16 +156,32 @@ __global__ void __launch_bounds__(kBThreads, 3) k_bstream(const double* const* _
     bad = 0;
   };
 
+  extern __shared__ uint4 s_bring[];
+  uint4* ring = STAGED ? s_bring + (threadIdx.x >> 5) * (2 * kStageWords) : nullptr;
   long long gg = g0;
   int p = find_pair(gpre, count, g0);
   Chunk cur, nxt;
-  load_item<LOG2B>(xs[p], ys[p], ns[p], gg - gpre[p], lane, cur);
+  if (STAGED) {
+    issue_item<LOG2B>(xs[p], ys[p], ns[p], gg - gpre[p], lane, ring);
+    cp_async_commit();
+  } else {
+    load_item<LOG2B>(xs[p], ys[p], ns[p], gg - gpre[p], lane, cur);
+  }
+  int stage = 0;
   while (gg < g1) {
     // next item of this warp, possibly in the next pair
     const long long ngg = gg + 1;
     int np = p;
     while (np + 1 < count && ngg >= gpre[np + 1]) ++np;
-    if (ngg < g1) load_item<LOG2B>(xs[np], ys[np], ns[np], ngg - gpre[np], lane, nxt);
+    if (STAGED) {
+      if (ngg < g1) issue_item<LOG2B>(xs[np], ys[np], ns[np], ngg - gpre[np], lane, ring + (stage ^ 1) * kStageWords);
+      cp_async_commit();
+      cp_async_wait<1>();  // this lane's copies of item gg have landed
+      read_item<LOG2B>(ring + stage * kStageWords, ns[p], gg - gpre[p], lane, cur);
+      stage ^= 1;
+    } else if (ngg < g1) {
+      load_item<LOG2B>(xs[np], ys[np], ns[np], ngg - gpre[np], lane, nxt);
+    }
     long long aH = 0, aS = 0;
     double aD = 0.0;
     int M = 0, zeros = 0, u;
@@ -189,10 +207,11 @@ __global__ void __launch_bounds__(kBThreads, 3) k_bstream(const double* const* _
       if (sub < 4) reinterpret_cast<long long*>(recs + bpre[p] + lb)[sub] = word;
     }
     if (np != p) flush(p);
-    cur = nxt;
+    if (!STAGED) cur = nxt;
     gg = ngg;
     p = np;
   }
+  if (STAGED) cp_async_wait<0>();
   flush(p < count ? p : count - 1);
 }
 
@@ -281,10 +300,26 @@ BatchLayout batch_layout(int count) {
   return l;
 }
 
+template <int LOG2B, int THREADS, bool STAGED>
+cudaError_t launch_stream(int grid, const double* const* xs, const double* const* ys, const long long* ns, int count,
+                          const long long* gpre, const long long* bpre, PairStats* ps, const BatchHeader* hdr,
+                          BlockRec* recs, cudaStream_t st) {
+  const int smem = STAGED ? (THREADS / 32) * 2 * kStageWords * 16 : 0;
+  static bool attr_set = false;  // per instantiation
+  if (STAGED && !attr_set) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_bstream<LOG2B, THREADS, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_bstream<LOG2B, THREADS, STAGED><<<grid, THREADS, smem, st>>>(xs, ys, ns, count, gpre, bpre, ps, hdr, recs);
+  return cudaGetLastError();
+}
+
 template <int LOG2B>
 cudaError_t launch_batched_lb(const double* const* xs, const double* const* ys, const long long* ns, int count,
-                              const qdot_params* p, qdot_result* outs, int grid, char* ws, size_t ws_bytes,
-                              cudaStream_t st) {
+                              const qdot_params* p, qdot_result* outs, const qdot_batched_tuning& t, char* ws,
+                              size_t ws_bytes, cudaStream_t st) {
   const BatchLayout l = batch_layout(count);
   auto* hdr = reinterpret_cast<BatchHeader*>(ws + l.off_hdr);
   auto* gpre = reinterpret_cast<long long*>(ws + l.off_gpre);
@@ -293,10 +328,19 @@ cudaError_t launch_batched_lb(const double* const* xs, const double* const* ys, 
   auto* recs = reinterpret_cast<BlockRec*>(ws + l.off_rec);
   const long long capacity = (long long)((ws_bytes - l.fixed) / sizeof(BlockRec));
   k_bplan<<<1, 1024, 0, st>>>(xs, ys, ns, count, LOG2B, capacity, gpre, bpre, ps, hdr);
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const int grid = t.grid_ctas > 0 ? t.grid_ctas : t.ctas_per_sm * sms;
   cudaEvent_t ev0, ev1;
   kernel_events(&ev0, &ev1);
   if (ev0) cudaEventRecord(ev0, st);
-  k_bstream<LOG2B><<<grid, kBThreads, 0, st>>>(xs, ys, ns, count, gpre, bpre, ps, hdr, recs);
+  cudaError_t e;
+  if (t.threads_per_cta == 128)
+    e = t.staged ? launch_stream<LOG2B, 128, true>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, st)
+                 : launch_stream<LOG2B, 128, false>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, st);
+  else
+    e = t.staged ? launch_stream<LOG2B, 256, true>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, st)
+                 : launch_stream<LOG2B, 256, false>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, st);
+  if (e != cudaSuccess) return e;
   if (ev1) cudaEventRecord(ev1, st);
   k_bfinal<<<count, 256, 0, st>>>(ns, bpre, ps, hdr, recs, LOG2B, *p, outs);
   return cudaGetLastError();
@@ -310,19 +354,21 @@ size_t batched_ws_bytes(const int64_t* ns_host, int count, const qdot_params* p)
   return batch_layout(count).fixed + align_up(sizeof(chunk::BlockRec) * (size_t)blocks, 256);
 }
 
+qdot_batched_tuning default_batched_tuning() { return qdot_batched_tuning{256, 3, 0, 1}; }
+
 cudaError_t launch_qdot_batched(const double* const* xs, const double* const* ys, const long long* ns, int count,
                                 const qdot_params* p, qdot_result* outs, int grid_ctas, void* ws, size_t ws_bytes,
-                                cudaStream_t st) {
-  const int sms = device_info().sms > 0 ? device_info().sms : 152;
-  const int grid = grid_ctas > 0 ? grid_ctas : 3 * sms;
+                                cudaStream_t st, const qdot_batched_tuning* tuning) {
+  qdot_batched_tuning t = tuning ? *tuning : default_batched_tuning();
+  if (grid_ctas > 0) t.grid_ctas = grid_ctas;
   int lb = 0;
   while ((1 << lb) < p->block) ++lb;
   char* w = static_cast<char*>(ws);
   switch (lb) {
-    case 5: return launch_batched_lb<5>(xs, ys, ns, count, p, outs, grid, w, ws_bytes, st);
-    case 6: return launch_batched_lb<6>(xs, ys, ns, count, p, outs, grid, w, ws_bytes, st);
-    case 7: return launch_batched_lb<7>(xs, ys, ns, count, p, outs, grid, w, ws_bytes, st);
-    default: return launch_batched_lb<8>(xs, ys, ns, count, p, outs, grid, w, ws_bytes, st);
+    case 5: return launch_batched_lb<5>(xs, ys, ns, count, p, outs, t, w, ws_bytes, st);
+    case 6: return launch_batched_lb<6>(xs, ys, ns, count, p, outs, t, w, ws_bytes, st);
+    case 7: return launch_batched_lb<7>(xs, ys, ns, count, p, outs, t, w, ws_bytes, st);
+    default: return launch_batched_lb<8>(xs, ys, ns, count, p, outs, t, w, ws_bytes, st);
   }
 }
 
@@ -341,9 +387,9 @@ size_t qdot_batched_workspace_size(const int64_t* ns_host, int32_t count, const 
   return batched_ws_bytes(ns_host, count, p);
 }
 
-qdot_status qdot_batched(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
-                         const qdot_params* p, qdot_result* outs, int32_t grid_ctas, void* ws, size_t ws_bytes,
-                         void* stream) {
+qdot_status qdot_batched_tuned(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
+                               const qdot_params* p, qdot_result* outs, const qdot_batched_tuning* tuning,
+                               int32_t grid_ctas, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
   std::string why;
   if (!p || !valid_params(0, p, &why)) {
@@ -368,14 +414,27 @@ qdot_status qdot_batched(const double* const* xs, const double* const* ys, const
     set_error("qdot_batched: workspace missing, misaligned or smaller than qdot_batched_workspace_size()");
     return QDOT_ERR_WORKSPACE;
   }
+  if (tuning && !((tuning->threads_per_cta == 128 || tuning->threads_per_cta == 256) &&
+                  (tuning->staged == 0 || tuning->staged == 1) && tuning->grid_ctas >= 0 &&
+                  (tuning->grid_ctas > 0 || (tuning->ctas_per_sm >= 1 && tuning->ctas_per_sm <= 64)))) {
+    set_error("qdot_batched: tuning needs threads_per_cta 128 or 256, staged 0 or 1, and grid_ctas > 0 or "
+              "ctas_per_sm in [1, 64]");
+    return QDOT_ERR_ARG;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long* nsl = reinterpret_cast<const long long*>(ns);
-  const cudaError_t e = launch_qdot_batched(xs, ys, nsl, count, p, outs, grid_ctas, ws, ws_bytes, st);
+  const cudaError_t e = launch_qdot_batched(xs, ys, nsl, count, p, outs, grid_ctas, ws, ws_bytes, st, tuning);
   if (e != cudaSuccess) {
     set_error(std::string("qdot_batched launch: ") + cudaGetErrorString(e));
     return QDOT_ERR_CUDA;
   }
   return QDOT_OK;
+}
+
+qdot_status qdot_batched(const double* const* xs, const double* const* ys, const int64_t* ns, int32_t count,
+                         const qdot_params* p, qdot_result* outs, int32_t grid_ctas, void* ws, size_t ws_bytes,
+                         void* stream) {
+  return qdot_batched_tuned(xs, ys, ns, count, p, outs, nullptr, grid_ctas, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

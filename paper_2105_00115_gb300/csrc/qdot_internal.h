@@ -80,7 +80,7 @@ cudaError_t launch_qdot_auto(const double* x, const double* y, int64_t n, const 
 size_t batched_ws_bytes(const int64_t* ns_host, int count, const qdot_params* p);
 cudaError_t launch_qdot_batched(const double* const* xs, const double* const* ys, const long long* ns, int count,
                                 const qdot_params* p, qdot_result* outs, int grid_ctas, void* ws, size_t ws_bytes,
-                                cudaStream_t stream);
+                                cudaStream_t stream, const qdot_batched_tuning* tuning = nullptr);
 
 // Plain FP64 dot.
 cudaError_t launch_dot_fp64(const double* x, const double* y, int64_t n, double* out, void* ws,

@@ -95,3 +95,32 @@ def test_batched_graph_replay_and_bad_pair(q, orc):
     rm = bm.results()
     assert rm[1].status == 1
     assert rm[0].count == first[0].count and rm[2].count == first[3].count
+
+
+def test_every_launch_shape_gives_the_same_results(q, orc, tmp_path):
+    import numpy as np
+    import torch
+    from paper_2105_00115_gb300 import _abi, tune
+    lengths = [0, 1, 255, 256, 257, 4096, 70001, 33, 1 << 16]
+    xs, ys, ref = [], [], []
+    for i, n in enumerate(lengths):
+        x, y = workloads.pair("b", n, 300 + i)
+        xs.append(torch.from_numpy(x).cuda())
+        ys.append(torch.from_numpy(y).cuda())
+        ref.append(orc.qdot(x, y, eps=1e-8, block=64))
+    batch = q.Batch(xs, ys, eps=1e-8, block=64)
+    seen = set()
+    for threads, ctas, staged in tune.CANDIDATES:
+        batch.tuning = _abi.BatchedTuning(threads, ctas, 0, staged)
+        batch.launch()
+        res = batch.results()
+        seen.add(tuple(r.value for r in res))
+        for r, o, x in zip(res, ref, xs):
+            assert r.count == tuple(o.count)
+    assert len(seen) == 1  # identical values for every launch shape
+    tuning, times = batch.autotune(reps=2, path=str(tmp_path / "t.json"))
+    assert (tuning.threads_per_cta, tuning.ctas_per_sm, tuning.staged) in tune.CANDIDATES
+    assert len(times) == len(tune.CANDIDATES)
+    tuning2, _ = batch.autotune(reps=2, path=str(tmp_path / "t.json"))  # from the cache
+    assert (tuning2.threads_per_cta, tuning2.ctas_per_sm, tuning2.staged) == \
+        (tuning.threads_per_cta, tuning.ctas_per_sm, tuning.staged)
