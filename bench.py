@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-1e-10 summary of the single line")
     ap.add_argument("--grid", type=int, default=128, help="CG grid edge (cg workload)")
     ap.add_argument("--eps-sweep", action="store_true", help="cg workload: ACG at eps = 1e-16 .. 1e3")
+    ap.add_argument("--sweep", action="store_true",
+                    help="single workload: time every block in {1, 32, 256} x eps in {1e-15, 1e-8, 1e-1} on the "
+                         "same data and print one JSON line with the table")
     ap.add_argument("--pairs", type=int, default=4096)
     ap.add_argument("--grid-ctas", type=int, default=0)
     return ap.parse_args()
@@ -548,6 +551,48 @@ def run_backward(args, rank, world, local, dist, lib):
     }
 
 
+def run_sweep(args, xd, yd, lib, dist):
+    """Config-2 table: every (block, eps) cell on the same resident data."""
+    import torch
+
+    import paper_2105_00115_gb300 as q
+    n = xd.numel()
+    stream = torch.cuda.current_stream()
+    peak, peak_src = measured_peak_hbm()
+    out = torch.empty(80, dtype=torch.uint8, device="cuda")
+    cells = []
+    for block in (1, 32, 256):
+        for eps in (1e-15, 1e-8, 1e-1):
+            p = q.params(eps, block, 1, 0, "auto")
+            ws = torch.empty(max(lib.qdot_workspace_size(n, ctypes.byref(p)), 256), dtype=torch.uint8, device="cuda")
+            for _ in range(3):
+                q.qdot_async(xd, yd, eps, block, 1, 0, "auto", out=out, ws=ws, stream=stream)
+            kb, ke = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            kb.record(stream)
+            ke.record(stream)
+            steps, kms = [], []
+            for _ in range(args.steps):
+                t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                lib.qdot_set_kernel_events(ctypes.c_void_p(kb.cuda_event), ctypes.c_void_p(ke.cuda_event))
+                t0.record(stream)
+                q.qdot_async(xd, yd, eps, block, 1, 0, "auto", out=out, ws=ws, stream=stream)
+                t1.record(stream)
+                lib.qdot_set_kernel_events(None, None)
+                torch.cuda.synchronize()
+                steps.append(t0.elapsed_time(t1))
+                kms.append(kb.elapsed_time(ke))
+            r = q.decode_result(out.cpu().numpy())
+            step_ms = dist.max(statistics.median(steps))
+            kern_ms = dist.max(statistics.median(kms))
+            path = "one_pass" if lib.qdot_select_path(n, ctypes.byref(p), 1) == 2 else "two_pass"
+            cells.append({"block": block, "eps": eps, "path": path, "step_gbs": 16.0 * n / (step_ms * 1e-3) / 1e9,
+                          "kernel_gbs": 16.0 * n / (kern_ms * 1e-3) / 1e9,
+                          "step_frac": 16.0 * n / (step_ms * 1e-3) / 1e9 / peak, "count": list(r.count)})
+            del ws
+    return {"metric": METRIC, "sweep": cells, "n": n, "distribution": DIST_NAMES[args.dist], "peak": peak,
+            "peak_source": peak_src, "steps": args.steps}
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -575,6 +620,15 @@ def main():
         return
     n = args.n
     x, y = workloads.pair(args.dist, n, 2106 + rank)
+    if args.sweep:
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.from_numpy(y).cuda()
+        del x, y
+        line = run_sweep(args, xd, yd, lib, dist)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        dist.close()
+        return
     xd = torch.from_numpy(x).cuda()
     yd = torch.from_numpy(y).cuda()
     stream = torch.cuda.current_stream()

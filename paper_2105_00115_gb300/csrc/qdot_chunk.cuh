@@ -243,32 +243,56 @@ __device__ __forceinline__ bool chunk_keys(const Chunk& ch, int (&key)[8], int& 
   return plain;
 }
 
+// The bit pattern of a double with its significand rounded to 52 - K
+// fraction bits, ties to even (K = 29: SINGLE, K = 42: HALF); a carry out
+// of the fraction moves into the exponent field.
+template <int K>
+__device__ __forceinline__ uint64_t round_bits(uint64_t v) {
+  return (v + ((1ull << (K - 1)) - 1ull) + ((v >> K) & 1ull)) & ~((1ull << K) - 1ull);
+}
+
 // Candidates of the plain path for the classes in MASK, with u the block's
-// maximum key (biased).
+// maximum key (biased).  The highest class in MASK goes through the FP64
+// pipe: one fused multiply-add of the exponent-rescaled operands (rounded to
+// that class's precision first, so the product is exact for HALF and
+// SINGLE) into aF; the other classes use the 64-bit integer path into aH /
+// aS.  The FP64 pipe sustains about one fused multiply-add per component at
+// full bandwidth, so only one class takes it.
 template <int LOG2B, unsigned MASK>
 __device__ __forceinline__ void acc_fast(const Chunk& ch, const int (&key)[8], int u, long long& aH, long long& aS,
-                                         double& aD) {
+                                         double& aF) {
   constexpr int K = LOG2B;
+  constexpr unsigned TOP = (MASK & kCandD) ? kCandD : ((MASK & kCandS) ? kCandS : kCandH);
+  constexpr unsigned INT_MASK = MASK & (kCandH | kCandS) & ~TOP;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint32_t hx = (uint32_t)(ch.x[j] >> 32), lx = (uint32_t)ch.x[j];
     const uint32_t hy = (uint32_t)(ch.y[j] >> 32), ly = (uint32_t)ch.y[j];
     const int d = u - key[j];
-    if (MASK & (kCandH | kCandS)) {
+    if (INT_MASK) {
       const uint32_t mx = (hx & 0xFFFFFu) | 0x100000u, my = (hy & 0xFFFFFu) | 0x100000u;
       const int sgn = product_sign(hx, hy);
-      if (MASK & kCandH) {
+      if (INT_MASK & kCandH) {
         const int yh = (int)half_sig(my, ly) * sgn;
         aH += sar64((long long)((int)half_sig(mx, lx) * yh) << (40 - K), d);
       }
-      if (MASK & kCandS) {
+      if (INT_MASK & kCandS) {
         const int ys = (int)single_sig(my, ly) * (sgn * 64);
         aS += sar64((long long)(int)single_sig(mx, lx) * (long long)ys, d);
       }
     }
-    if (MASK & kCandD) {
+    if (MASK) {
       const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
-      aD = fma(make_double((hx & 0x800FFFFFu) | 0x3FF00000u, lx), make_double((hy & 0x800FFFFFu) | ye, ly), aD);
+      uint64_t xo = ((uint64_t)((hx & 0x800FFFFFu) | 0x3FF00000u) << 32) | lx;
+      uint64_t yo = ((uint64_t)((hy & 0x800FFFFFu) | ye) << 32) | ly;
+      if (TOP == kCandS) {
+        xo = round_bits<29>(xo);
+        yo = round_bits<29>(yo);
+      } else if (TOP == kCandH) {
+        xo = round_bits<42>(xo);
+        yo = round_bits<42>(yo);
+      }
+      aF = fma(__longlong_as_double((long long)xo), __longlong_as_double((long long)yo), aF);
     }
   }
 }
@@ -379,13 +403,21 @@ __device__ __forceinline__ long long block_record_word(long long aH, long long a
 // u_b = s_b - ceil(log2 M_b).
 constexpr int kMetaKeyBias = 4096;
 
+// aF holds the candidate of class `top` (kCand*): D or H on the grid
+// 2^(u - 60 + K), S on 2^(u - 52).
 template <int LOG2B>
-__device__ __forceinline__ void block_record_compact(long long aH, long long aS, double aD, int M, int u_b,
-                                                     unsigned stored, int sub, int* key_out, int* u_out,
+__device__ __forceinline__ void block_record_compact(long long aH, long long aS, double aF, unsigned top, int M,
+                                                     int u_b, unsigned stored, int sub, int* key_out, int* u_out,
                                                      int* m_out, long long* slot, unsigned* meta,
                                                      long long* half_out) {
   constexpr int L = Map<LOG2B>::L;
-  long long aDi = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
+  long long aDi = 0;
+  if (top == kCandS)
+    aS = __double2ll_rz(aF * 4503599627370496.0);  // 2^52
+  else if (top == kCandH)
+    aH = __double2ll_rz(aF * (double)(1ll << (60 - LOG2B)));
+  else
+    aDi = __double2ll_rz(aF * (double)(1ll << (60 - LOG2B)));
   aH = group_sum<L>(aH);
   aS = group_sum<L>(aS);
   aDi = group_sum<L>(aDi);
@@ -457,6 +489,28 @@ __device__ long long recompute_candidate(const double* __restrict__ x, const dou
   if (cls == kHalf) return aH;
   if (cls == kSingle) return aS;
   return __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
+}
+
+// recompute_candidate() by one warp: lane l takes components l, l + 32, ...;
+// the H / S partial sums add exactly, each lane's D partial is moved to the
+// grid before the sum.  Every lane returns the total.
+template <int LOG2B>
+__device__ long long recompute_candidate_warp(const double* __restrict__ x, const double* __restrict__ y,
+                                              long long n, long long blk, int u, int cls, int lane) {
+  const long long lo = blk << LOG2B, hi = min(n, lo + (1ll << LOG2B));
+  long long aH = 0, aS = 0;
+  double aD = 0.0;
+  const unsigned mask = 1u << cls;
+  for (long long i = lo + lane; i < hi; i += 32) {
+    const uint64_t a = (uint64_t)__double_as_longlong(x[i]), b = (uint64_t)__double_as_longlong(y[i]);
+    if (is_zero(a) || is_zero(b)) continue;
+    const int e = exponent_of(a) + exponent_of(b) + 2046;
+    component_candidates<LOG2B>(a, b, e, u + 2046, mask, aH, aS, aD);
+  }
+  long long v = cls == kHalf ? aH : (cls == kSingle ? aS : __double2ll_rz(aD * (double)(1ll << (60 - LOG2B))));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 }  // namespace chunk

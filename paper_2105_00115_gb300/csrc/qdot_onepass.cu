@@ -72,6 +72,9 @@ struct OpPart {
 // two items get every candidate.
 constexpr int kWinS = 6, kWinH = 5, kWinEarly = 8;
 
+// Blocks a gather CTA can queue for recomputation by its warps together.
+constexpr int kRepairQueue = 512;
+
 // The candidates a block with maximum key u (biased; kNone if empty) should
 // get, after folding u into the warp's running bound e_lo of e_max.  e_lo
 // also takes in erun, the bound shared by all warps: read at item 1 (used at
@@ -156,14 +159,16 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
     long long aH = 0, aS = 0;
     double aD = 0.0;
     int M = 0, zeros = 0, u;
-    unsigned want = 0;
+    unsigned want = 0, top = kCandD;  // top: the class aD holds (the general path computes D there)
     int key[8];
     int cmax = kNone;
     if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
       u = group_max<L>(cmax);
       M = 8;
       want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
-      acc_fast_mask<LOG2B>(__reduce_or_sync(0xffffffffu, want), cur, key, u, aH, aS, aD);
+      const unsigned cands = __reduce_or_sync(0xffffffffu, want);
+      top = cands ? (1u << (31 - __clz((int)cands))) : kCandD;
+      acc_fast_mask<LOG2B>(cands, cur, key, u, aH, aS, aD);
     } else {
       u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);  // every candidate
       want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
     int kb, ub, mb;
     long long slot, half;
     unsigned meta;
-    block_record_compact<LOG2B>(aH, aS, aD, M, u, want, sub, &kb, &ub, &mb, &slot, &meta, &half);
+    block_record_compact<LOG2B>(aH, aS, aD, top, M, u, want, sub, &kb, &ub, &mb, &slot, &meta, &half);
     const long long blk = it * BPI + g;
     zeros_l += zeros;
     if (blk < nblocks) {
@@ -290,8 +295,12 @@ __global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__
   __shared__ uint8_t s_lut[kKeyCount];
   __shared__ i128 s_sum[8];
   __shared__ unsigned long long s_cnt[8][5];
+  __shared__ long long s_qblk[kRepairQueue];  // blocks to recompute ...
+  __shared__ int s_qinfo[kRepairQueue];       // ... with u << 2 | class
+  __shared__ int s_nqueue;
   for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
     reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
+  if (threadIdx.x == 0) s_nqueue = 0;
   __syncthreads();
   const int lsb = hdr->lsb;
   const bool ok = hdr->status == QDOT_OK;
@@ -336,17 +345,34 @@ __global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__
         v[k] = (stored == kCandAll && cls == kHalf) ? slot3[b0 + k]  // b0 + k < n_early by construction
                                                     : slots[2 * (b0 + k) + (cls == top ? 0 : 1)];
       } else {
-        v[k] = recompute_candidate<LOG2B>(x, y, n, b0 + k, uu[k], cls);
         ++c[4];
+        const int slot = atomicAdd(&s_nqueue, 1);
+        if (slot < kRepairQueue) {  // the CTA's warps recompute it together after the sweep
+          s_qblk[slot] = b0 + k;
+          s_qinfo[slot] = (uu[k] << 2) | cls;
+          cl[k] = kPerf;
+        } else {  // queue full: this thread recomputes it alone
+          v[k] = recompute_candidate<LOG2B>(x, y, n, b0 + k, uu[k], cls);
+        }
       }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (cl[k] != kPerf) acc += candidate_to_fixed(v[k], cl[k], uu[k], LOG2B, lsb);
   }
+  // queued recomputations: one warp per block, lanes striding over its
+  // components (coalesced), partial candidates summed over the warp
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nq = min(s_nqueue, kRepairQueue);
+  for (int qi = w; qi < nq; qi += (int)(blockDim.x >> 5)) {
+    const long long blk = s_qblk[qi];
+    const int cls = s_qinfo[qi] & 3, u = s_qinfo[qi] >> 2;
+    const long long v = recompute_candidate_warp<LOG2B>(x, y, n, blk, u, cls, lane);
+    if (lane == 0) acc += candidate_to_fixed(v, cls, u, LOG2B, lsb);
+  }
   acc = warp_sum_i128(acc);
   for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     s_sum[w] = acc;
     for (int k = 0; k < 5; ++k) s_cnt[w][k] = c[k];
