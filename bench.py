@@ -730,7 +730,7 @@ def main():
         cg = cg_summary(args)
 
     peak, peak_src = measured_peak_hbm()
-    kernel = "k_onepass" if lib.qdot_select_path(n, ctypes.byref(p), 1) == 2 else "k_apply"
+    kernel = {2: "k_onepass", 4: "k_qdot_fused"}.get(lib.qdot_select_path(n, ctypes.byref(p), 1), "k_apply_fast")
     achieved = 16.0 * n / (kern_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

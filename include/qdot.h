@@ -73,14 +73,18 @@ enum { QDOT_PERF = 0, QDOT_HALF = 1, QDOT_SINGLE = 2, QDOT_DOUBLE = 3, QDOT_ZERO
 enum { QDOT_PATH_AUTO = 0, QDOT_PATH_TWO_PASS = 1, QDOT_PATH_ONE_PASS = 2,
        /* qdot_cg / qdot_power only: every dot product a plain FP64 dot (the
         * comparator); eps, block, split_budget and mant_reading are ignored */
-       QDOT_PATH_FP64_DOT = 3 };
+       QDOT_PATH_FP64_DOT = 3,
+       /* one cooperative launch (32 <= B <= 256, 16-byte aligned, n up to
+        * 16 warps x 8 items x 256 per SM, about 5 million on a 152-SM GPU);
+        * AUTO takes it when it applies */
+       QDOT_PATH_FUSED = 4 };
 
 typedef struct {
   double eps;           /* qdot tolerance eps > 0, finite (Algorithm 3 input) */
   int32_t block;        /* 0: exact binning; else B, a power of two in [1, 2^20] */
   int32_t split_budget; /* 1: eps / N_bins (default, Sec. 4.1); 0: eps (eq. bin-score-def) */
   int32_t mant_reading; /* 0: m_half, m_single = 10, 23 (default); 1: 11, 24 */
-  int32_t path;         /* QDOT_PATH_*; the one-pass path needs 32 <= B <= 256 */
+  int32_t path;         /* QDOT_PATH_*; the one-pass and fused paths need 32 <= B <= 256 */
 } qdot_params;
 
 /* Device-side result of one qdot (80 bytes). */
@@ -316,8 +320,8 @@ qdot_status qdot_static_scratch(const double* x, const double* y, int64_t n, con
  * invalid parameters); `aligned16` tells whether x and y are 16-byte aligned. */
 int32_t qdot_kernel_launches(int64_t n, const qdot_params* p, int32_t aligned16);
 
-/* The path qdot() takes for these arguments: QDOT_PATH_ONE_PASS or
- * QDOT_PATH_TWO_PASS (0 on invalid parameters). */
+/* The path qdot() takes for these arguments: QDOT_PATH_FUSED,
+ * QDOT_PATH_ONE_PASS or QDOT_PATH_TWO_PASS (0 on invalid parameters). */
 int32_t qdot_select_path(int64_t n, const qdot_params* p, int32_t aligned16);
 
 /* Measurement hook.  When begin and end are both non-NULL (cudaEvent_t

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(_PKG, "libqdot.so")
 
 KEY_MIN = -2148
 KEY_COUNT = 4224
-PATHS = {"auto": 0, "two_pass": 1, "one_pass": 2, "fp64_dot": 3}
+PATHS = {"auto": 0, "two_pass": 1, "one_pass": 2, "fp64_dot": 3, "fused": 4}
 STATUS = {0: "QDOT_OK", 1: "QDOT_ERR_ARG", 2: "QDOT_ERR_NONFINITE", 3: "QDOT_ERR_CUDA", 4: "QDOT_ERR_TIMEOUT",
           5: "QDOT_ERR_WORKSPACE", 6: "QDOT_ERR_NOCONV"}
 

@@ -68,8 +68,8 @@ bool valid_params(int64_t n, const qdot_params* p, std::string* why) {
     *why = "mant_reading must be 0 or 1";
     return false;
   }
-  if (p->path < QDOT_PATH_AUTO || p->path > QDOT_PATH_ONE_PASS) {
-    *why = "path must be QDOT_PATH_AUTO, QDOT_PATH_TWO_PASS or QDOT_PATH_ONE_PASS";
+  if (p->path < QDOT_PATH_AUTO || p->path > QDOT_PATH_FUSED || p->path == QDOT_PATH_FP64_DOT) {
+    *why = "path must be QDOT_PATH_AUTO, QDOT_PATH_TWO_PASS, QDOT_PATH_ONE_PASS or QDOT_PATH_FUSED";
     return false;
   }
   return true;
@@ -85,18 +85,21 @@ using namespace qd;
 
 namespace {
 
-enum PathChoice { kTwoPass, kOnePass };
+enum PathChoice { kTwoPass, kOnePass, kFused };
 
 PathChoice choose_path(int64_t n, const qdot_params* p, bool al16) {
   if (p->path == QDOT_PATH_TWO_PASS) return kTwoPass;
-  bool ok = one_pass_supported(n, p, al16);
-  if (p->path == QDOT_PATH_ONE_PASS) return ok ? kOnePass : kTwoPass;
-  return ok ? kOnePass : kTwoPass;
+  const bool one = one_pass_supported(n, p, al16);
+  if (p->path == QDOT_PATH_ONE_PASS) return one ? kOnePass : kTwoPass;
+  const bool fused = fused_supported(n, p, al16);
+  if (p->path == QDOT_PATH_FUSED) return fused ? kFused : (one ? kOnePass : kTwoPass);
+  return fused ? kFused : (one ? kOnePass : kTwoPass);
 }
 
 size_t workspace_for(int64_t n, const qdot_params* p, bool al16, PathChoice* choice) {
   PathChoice c = choose_path(n, p, al16);
   if (choice) *choice = c;
+  if (c == kFused) return fused_ws_bytes();
   if (c == kOnePass) return plan_one_pass(n, p).total;
   return plan_two_pass(n, p, al16).total;
 }
@@ -142,6 +145,7 @@ cudaError_t launch_qdot_auto(const double* x, const double* y, int64_t n, const 
                              qdot_result* out, cudaStream_t st) {
   const bool al16 = aligned16(x, y);
   PathChoice c = choose_path(n, p, al16);
+  if (c == kFused) return launch_fused(x, y, n, p, ws, out, nullptr, st);
   if (c == kOnePass) return launch_one_pass(x, y, n, p, plan_one_pass(n, p), ws, out, nullptr, st);
   return launch_two_pass(x, y, n, p, plan_two_pass(n, p, al16), ws, out, nullptr, nullptr, nullptr, nullptr, st);
 }
@@ -170,7 +174,9 @@ qdot_status qdot(const double* x, const double* y, int64_t n, const qdot_params*
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (c == kOnePass)
+  if (c == kFused)
+    e = launch_fused(x, y, n, p, ws, out, sel, st);
+  else if (c == kOnePass)
     e = launch_one_pass(x, y, n, p, plan_one_pass(n, p), ws, out, sel, st);
   else
     e = launch_two_pass(x, y, n, p, plan_two_pass(n, p, al16), ws, out, sel, nullptr, nullptr, nullptr, st);
@@ -251,6 +257,7 @@ int32_t qdot_kernel_launches(int64_t n, const qdot_params* p, int32_t al16) {
   std::string why;
   if (!valid_params(n, p, &why)) return 0;
   PathChoice c = choose_path(n, p, al16 != 0);
+  if (c == kFused) return 1;
   if (c == kOnePass) return one_pass_launches(n, p);
   return 4;  // stats, select, apply, final
 }
@@ -258,7 +265,8 @@ int32_t qdot_kernel_launches(int64_t n, const qdot_params* p, int32_t al16) {
 int32_t qdot_select_path(int64_t n, const qdot_params* p, int32_t al16) {
   std::string why;
   if (!valid_params(n, p, &why)) return 0;
-  return choose_path(n, p, al16 != 0) == kOnePass ? QDOT_PATH_ONE_PASS : QDOT_PATH_TWO_PASS;
+  const PathChoice c = choose_path(n, p, al16 != 0);
+  return c == kFused ? QDOT_PATH_FUSED : (c == kOnePass ? QDOT_PATH_ONE_PASS : QDOT_PATH_TWO_PASS);
 }
 
 void qdot_set_kernel_events(void* begin, void* end) {

@@ -1,0 +1,351 @@
+// qdot in one launch for vectors that the resident grid covers in a few
+// warp items (the sizes of the solvers' dot products: 2^21 .. 2^23).
+//
+// At these sizes the multi-kernel paths spend most of their time in launch
+// gaps and one-CTA kernels.  Here one cooperative launch does everything:
+//   phase 1  every warp streams its items (at most kFusedItems) and keeps, per
+//            block, the exact HALF / SINGLE / DOUBLE candidates, the block
+//            key and M_b in shared memory (blocked binning, 32 <= B <= 256);
+//            per-CTA statistics go to the workspace;
+//   sync     grid-wide barrier;
+//   phase 2  every CTA reduces the statistics (e_max, N_bins, f exactly), then
+//            classes its own blocks (eq. bin-score-def, eq. precision-def) and
+//            sums their chosen candidates exactly;
+//   phase 3  the last CTA to finish phase 2 (an arrival counter) adds the
+//            per-CTA sums in order and rounds once.
+// The values are those of the one-pass path (same candidates and grids).
+#include <climits>
+#include <cooperative_groups.h>
+
+#include "qdot_chunk.cuh"
+#include "qdot_common.cuh"
+#include "qdot_internal.h"
+
+namespace qd {
+namespace {
+
+using namespace chunk;
+namespace cgrp = cooperative_groups;
+
+constexpr int kFusedThreads = 256;
+constexpr int kFusedWarps = kFusedThreads / 32;
+constexpr int kFusedItems = 8;    // items per warp at most
+constexpr int kFusedCtasPerSm = 2;
+
+struct FusedBlock {  // one block's candidates (in shared memory)
+  long long h, s, d;
+  int key;           // s_b, kEmptyKey when the block has no nonzero component
+  unsigned m;        // M_b
+};
+
+struct CtaStats {
+  int e_max, e_min, bad, pad;
+  long long nbins, zeros;
+};
+
+struct FusedPart {
+  i128 sum;
+  unsigned long long cnt[4];
+};
+
+template <int LOG2B>
+__global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm)
+    k_qdot_fused(const double* __restrict__ x, const double* __restrict__ y, long long n, qdot_params prm,
+                 CtaStats* __restrict__ cstats, FusedPart* __restrict__ parts, unsigned* __restrict__ arrivals,
+                 qdot_selection* __restrict__ sel, qdot_result* __restrict__ out) {
+  constexpr int L = Map<LOG2B>::L, BPI = Map<LOG2B>::BPI;
+  __shared__ FusedBlock s_blk[kFusedWarps][kFusedItems][BPI];
+  __shared__ CtaStats s_w[kFusedWarps];
+  __shared__ i128 s_sum[kFusedWarps];
+  __shared__ unsigned long long s_cnt[kFusedWarps][4];
+  __shared__ int s_emax, s_emin, s_bad, s_f;
+  __shared__ long long s_nbins, s_zeros;
+  cgrp::grid_group grid = cgrp::this_grid();
+
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane / L, sub = lane % L;
+  const long long nblocks = (n + (1ll << LOG2B) - 1) >> LOG2B;
+  const long long nitems = (n + kItem - 1) / kItem;
+  const long long gwarp = (long long)blockIdx.x * kFusedWarps + w;
+  const long long nwarps = (long long)gridDim.x * kFusedWarps;
+
+  // ---- phase 1: stream ----
+  if (blockIdx.x == 0 && threadIdx.x == 0) *arrivals = 0;  // ordered before phase 2 by the grid barrier
+  long long nbins = 0, zeros_l = 0;
+  int emax_l = kNone, kmin = INT_MAX, bad = 0;
+  int k = 0;
+  Chunk cur, nxt;
+  if (gwarp < nitems) load_item<LOG2B>(x, y, n, gwarp, lane, cur);
+  for (long long it = gwarp; it < nitems && k < kFusedItems; it += nwarps, ++k) {
+    if (it + nwarps < nitems) load_item<LOG2B>(x, y, n, it + nwarps, lane, nxt);
+    long long aH = 0, aS = 0;
+    double aD = 0.0;
+    int M = 0, zeros = 0, u;
+    int key[8];
+    int cmax = kNone;
+    if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
+      u = group_max<L>(cmax);
+      M = 8;
+      acc_fast<LOG2B, kCandAll>(cur, key, u, aH, aS, aD);
+    } else {
+      u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);
+    }
+    int kb, ub, mb;
+    long long hv = 0, sv = 0, dv = 0;
+    {
+      long long aDi = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
+      hv = group_sum<L>(aH);
+      sv = group_sum<L>(aS);
+      dv = group_sum<L>(aDi);
+      mb = group_sum_i<L>(M);
+      ub = u - 2046;
+      kb = mb > 0 ? ceil_log2_u32((uint32_t)mb) + ub : (int)kEmptyKey;
+    }
+    const long long blk = it * BPI + g;
+    zeros_l += zeros;
+    const bool real = blk < nblocks && mb > 0;
+    if (real) {
+      nbins += (sub == 0);
+      emax_l = max(emax_l, ub);
+    }
+    if (sub == 0) s_blk[w][k][g] = FusedBlock{hv, sv, dv, real ? kb : (int)kEmptyKey, (unsigned)mb};
+    cur = nxt;
+  }
+  emax_l = __reduce_max_sync(0xffffffffu, emax_l);
+  kmin = __reduce_min_sync(0xffffffffu, kmin);
+  bad = (int)__reduce_or_sync(0xffffffffu, (unsigned)bad);
+  nbins = (long long)warp_sum_u64((unsigned long long)nbins);
+  zeros_l = (long long)warp_sum_u64((unsigned long long)zeros_l);
+  if (lane == 0) s_w[w] = CtaStats{emax_l, kmin == INT_MAX ? INT_MAX : kmin - 2046, bad, 0, nbins, zeros_l};
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    CtaStats c = s_w[0];
+    for (int i = 1; i < kFusedWarps; ++i) {
+      c.e_max = max(c.e_max, s_w[i].e_max);
+      c.e_min = min(c.e_min, s_w[i].e_min);
+      c.bad |= s_w[i].bad;
+      c.nbins += s_w[i].nbins;
+      c.zeros += s_w[i].zeros;
+    }
+    cstats[blockIdx.x] = c;
+  }
+  grid.sync();
+
+  // ---- phase 2: global statistics, classes, exact sums ----
+  {
+    int em = kNone, en = INT_MAX, bd = 0;
+    long long nb = 0, z = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kFusedThreads) {
+      const CtaStats c = cstats[i];
+      em = max(em, c.e_max);
+      en = min(en, c.e_min);
+      bd |= c.bad;
+      nb += c.nbins;
+      z += c.zeros;
+    }
+    em = __reduce_max_sync(0xffffffffu, em);
+    en = __reduce_min_sync(0xffffffffu, en);
+    bd = (int)__reduce_or_sync(0xffffffffu, (unsigned)bd);
+    nb = (long long)warp_sum_u64((unsigned long long)nb);
+    z = (long long)warp_sum_u64((unsigned long long)z);
+    if (lane == 0) s_w[w] = CtaStats{em, en, bd, 0, nb, z};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      CtaStats c = s_w[0];
+      for (int i = 1; i < kFusedWarps; ++i) {
+        c.e_max = max(c.e_max, s_w[i].e_max);
+        c.e_min = min(c.e_min, s_w[i].e_min);
+        c.bad |= s_w[i].bad;
+        c.nbins += s_w[i].nbins;
+        c.zeros += s_w[i].zeros;
+      }
+      if (c.nbins == 0) {
+        c.e_max = 0;
+        c.e_min = 0;
+      }
+      s_emax = c.e_max;
+      s_emin = c.e_min;
+      s_bad = c.bad;
+      s_nbins = c.nbins;
+      s_zeros = c.zeros;
+      s_f = c.nbins > 0 ? floor_log2_ratio(prm.eps, prm.split_budget ? (unsigned long long)c.nbins : 1ull) : 0;
+    }
+    __syncthreads();
+  }
+  const int e_max = s_emax, f = s_f;
+  const int mh = prm.mant_reading ? 11 : 10, ms = prm.mant_reading ? 24 : 23;
+  const int lsb = e_max - fixed_point_bits(n);
+  i128 acc = 0;
+  unsigned long long cnt[4] = {0, 0, 0, 0};
+  if (!s_bad && sub == 0) {
+    for (int kk = 0; kk < k; ++kk) {
+      const FusedBlock b = s_blk[w][kk][g];
+      if (b.key == (int)kEmptyKey) continue;
+      const int cls = precision_of((long long)b.key - e_max - f + 1, mh, ms);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cnt[c] += (cls == c) ? b.m : 0u;
+      const int u = b.key - ceil_log2_u32(b.m);
+      acc += record_candidate(b.h, b.s, b.d, u, cls, LOG2B, lsb);
+    }
+  }
+  acc = warp_sum_i128(acc);
+  for (int c = 0; c < 4; ++c) cnt[c] = warp_sum_u64(cnt[c]);
+  if (lane == 0) {
+    s_sum[w] = acc;
+    for (int c = 0; c < 4; ++c) s_cnt[w][c] = cnt[c];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    FusedPart p;
+    p.sum = 0;
+    for (int c = 0; c < 4; ++c) p.cnt[c] = 0;
+    for (int i = 0; i < kFusedWarps; ++i) {
+      p.sum += s_sum[i];
+      for (int c = 0; c < 4; ++c) p.cnt[c] += s_cnt[i][c];
+    }
+    parts[blockIdx.x] = p;
+  }
+  __shared__ bool s_last;
+  if (blockIdx.x == 0 && sel) {  // the parameter selection, for qdot_backward
+    for (int kk = threadIdx.x; kk < kKeyCount; kk += kFusedThreads)
+      sel->cls[kk] = (uint8_t)precision_of((long long)kKeyMin + kk - e_max - f + 1, mh, ms);
+    if (threadIdx.x == 0) {
+      sel->e_max = e_max;
+      sel->e_min = s_emin;
+      sel->f = f;
+      sel->status = s_bad ? QDOT_ERR_NONFINITE : QDOT_OK;
+      sel->n_bins = s_nbins;
+      sel->block = prm.block;
+      sel->key_min = kKeyMin;
+      sel->m_half = mh;
+      sel->m_single = ms;
+      sel->reserved[0] = sel->reserved[1] = 0;
+    }
+  }
+  // ---- phase 3: the last CTA to finish phase 2 adds the CTA sums in order ----
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's part is visible before its arrival counts
+    s_last = atomicAdd(arrivals, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  i128 tot = 0;
+  unsigned long long c4[4] = {0, 0, 0, 0};
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kFusedThreads) {
+    tot += parts[i].sum;
+    for (int c = 0; c < 4; ++c) c4[c] += parts[i].cnt[c];
+  }
+  tot = warp_sum_i128(tot);
+  for (int c = 0; c < 4; ++c) c4[c] = warp_sum_u64(c4[c]);
+  __syncthreads();  // s_sum / s_cnt are reused
+  if (lane == 0) {
+    s_sum[w] = tot;
+    for (int c = 0; c < 4; ++c) s_cnt[w][c] = c4[c];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < kFusedWarps; ++i) {
+      tot += s_sum[i];
+      for (int c = 0; c < 4; ++c) c4[c] += s_cnt[i][c];
+    }
+    // (tot and c4 in thread 0 already hold warp 0's totals)
+    qdot_result r;
+    r.status = s_bad ? QDOT_ERR_NONFINITE : QDOT_OK;
+    r.n_bins = s_nbins;
+    r.e_max = e_max;
+    r.e_min = s_emin;
+    r.f = f;
+    for (int c = 0; c < 4; ++c) r.count[c] = (int64_t)c4[c];
+    r.count[4] = s_zeros;
+    if (r.status != QDOT_OK) {
+      r.value = __longlong_as_double(0x7FF8000000000000ll);
+      r.bound = r.value;
+    } else {
+      r.value = fixed_to_double(tot, lsb);
+      r.bound = r.n_bins > 0 ? fixed_to_double((i128)r.n_bins, e_max + f) : 0.0;
+    }
+    *out = r;
+  }
+}
+
+// Grid of the fused launch on this device (co-resident CTAs), 0 if unknown.
+template <int LOG2B>
+int fused_grid() {
+  static int grid[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (grid[dev] == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qdot_fused<LOG2B>, kFusedThreads, 0) !=
+        cudaSuccess)
+      return 0;
+    const int sms = device_info().sms > 0 ? device_info().sms : 0;
+    grid[dev] = std::min(per_sm, kFusedCtasPerSm) * sms;
+  }
+  return grid[dev];
+}
+
+template <int LOG2B>
+cudaError_t launch_fused_lb(const double* x, const double* y, int64_t n, const qdot_params* p, char* ws,
+                            qdot_result* out, qdot_selection* sel, cudaStream_t st) {
+  const int grid = fused_grid<LOG2B>();
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  auto* cstats = reinterpret_cast<CtaStats*>(ws);
+  auto* parts = reinterpret_cast<FusedPart*>(ws + align_up(sizeof(CtaStats) * (size_t)grid, 256));
+  auto* arrivals = reinterpret_cast<unsigned*>(ws + align_up(sizeof(CtaStats) * (size_t)grid, 256) +
+                                               align_up(sizeof(FusedPart) * (size_t)grid, 256));
+  long long nn = n;
+  qdot_params prm = *p;
+  void* args[] = {(void*)&x,     (void*)&y,        (void*)&nn,  (void*)&prm, (void*)&cstats,
+                  (void*)&parts, (void*)&arrivals, (void*)&sel, (void*)&out};
+  cudaEvent_t ev0, ev1;
+  kernel_events(&ev0, &ev1);
+  if (ev0) cudaEventRecord(ev0, st);
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_qdot_fused<LOG2B>, dim3(grid),
+                                                    dim3(kFusedThreads), args, 0, st);
+  if (ev1) cudaEventRecord(ev1, st);
+  return e;
+}
+
+int fused_grid_for(int log2b) {
+  switch (log2b) {
+    case 5: return fused_grid<5>();
+    case 6: return fused_grid<6>();
+    case 7: return fused_grid<7>();
+    default: return fused_grid<8>();
+  }
+}
+
+}  // namespace
+
+bool fused_supported(int64_t n, const qdot_params* p, bool aligned16) {
+  if (!aligned16 || n <= 0 || p->block < 32 || p->block > 256) return false;
+  int lb = 0;
+  while ((1 << lb) < p->block) ++lb;
+  const int grid = fused_grid_for(lb);
+  if (grid <= 0) return false;
+  const long long nitems = (n + kItem - 1) / kItem;
+  return nitems <= (long long)grid * kFusedWarps * kFusedItems;
+}
+
+size_t fused_ws_bytes() {
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const size_t grid = (size_t)sms * kFusedCtasPerSm;
+  return align_up(sizeof(CtaStats) * grid, 256) + align_up(sizeof(FusedPart) * grid, 256) + 256;
+}
+
+cudaError_t launch_fused(const double* x, const double* y, int64_t n, const qdot_params* p, void* ws,
+                         qdot_result* out, qdot_selection* sel, cudaStream_t st) {
+  char* w = static_cast<char*>(ws);
+  int lb = 0;
+  while ((1 << lb) < p->block) ++lb;
+  switch (lb) {
+    case 5: return launch_fused_lb<5>(x, y, n, p, w, out, sel, st);
+    case 6: return launch_fused_lb<6>(x, y, n, p, w, out, sel, st);
+    case 7: return launch_fused_lb<7>(x, y, n, p, w, out, sel, st);
+    default: return launch_fused_lb<8>(x, y, n, p, w, out, sel, st);
+  }
+}
+
+}  // namespace qd

@@ -70,6 +70,13 @@ cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const q
                             const OnePassPlan& plan, void* ws, qdot_result* out, qdot_selection* sel,
                             cudaStream_t stream);
 
+// One-launch qdot for vectors the resident grid covers in a few items
+// (cooperative launch with grid-wide barriers).
+bool fused_supported(int64_t n, const qdot_params* p, bool aligned16);
+size_t fused_ws_bytes();
+cudaError_t launch_fused(const double* x, const double* y, int64_t n, const qdot_params* p, void* ws,
+                         qdot_result* out, qdot_selection* sel, cudaStream_t stream);
+
 // qdot() on device buffers with the path qdot() would choose (no checks);
 // ws must hold qdot_workspace_size(n, p) bytes.
 size_t qdot_ws_bytes(int64_t n, const qdot_params* p);

@@ -74,11 +74,15 @@ def test_closed_forms_gpu(q, orc, case):
 @pytest.mark.parametrize("block", [0, 1, 2, 4, 16, 32, 64, 128, 256, 1024])
 @pytest.mark.parametrize("kind", ["a", "b", "c", "cfg0"])
 def test_parity_grid(q, orc, kind, block):
+    # auto takes the fused launch for blocks of 32..256 at these sizes; the
+    # one-pass path is checked explicitly as well
+    paths = ("auto", "one_pass") if 32 <= block <= 256 else ("auto",)
     for n in (1, 63, 64, 65, 1000, 4097, 100003):
         x, y = workloads.pair(kind, n, 17 + n)
         for eps in (1e-16, 1e-8, 1e-3, 0.5):
             _check(q, orc, x, y, eps, block)
-            _check(q, orc, x, y, eps, block, explain=False)
+            for path in paths:
+                _check(q, orc, x, y, eps, block, explain=False, path=path)
 
 
 @pytest.mark.parametrize("block", [0, 1, 32, 256])
@@ -218,6 +222,25 @@ def test_one_pass_recompute_path(q, orc, block):
     assert r.count == tuple(ref.count)
     assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
     assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
+
+
+@pytest.mark.parametrize("block", [32, 64, 128, 256])
+def test_fused_path(q, orc, block):
+    """One cooperative launch (the solvers' sizes): parity with the oracle and
+    with the selection qdot() reports; the largest n it takes and one past."""
+    import ctypes
+    lib = q.load()
+    p = q.params(1e-8, block, 1, 0, "fused")
+    n_max = 0
+    for n in (257, 1 << 20, 2097152 + 3, 3 * 10**6 + 1):
+        x, y = workloads.pair("b", n, 7 + block)
+        assert lib.qdot_select_path(n, ctypes.byref(p), 1) == 4  # QDOT_PATH_FUSED
+        assert lib.qdot_kernel_launches(n, ctypes.byref(p), 1) == 1
+        for eps in (1e-15, 1e-8, 0.1):
+            _check(q, orc, x, y, eps, block, explain=False, path="fused")
+    # beyond the fused capacity the call falls back to the one-pass path
+    big = 1 << 25
+    assert lib.qdot_select_path(big, ctypes.byref(p), 1) == 2
 
 
 def test_deterministic_repeat(q, orc):
