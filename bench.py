@@ -298,7 +298,7 @@ def run_batched(args, rank, world, local, dist, lib):
         "config": {"workload": f"batched qdot, {len(sizes)} problems, n_j = floor(2^U(8,20)), {DIST_NAMES[args.dist]}, "
                                f"block={args.block}, eps={args.eps:g}, one CUDA graph replay per step",
                    "problems": len(sizes), "total_components": total, "block": args.block, "eps": args.eps,
-                   "l2": "inputs 8.3 GB per step > 129 MB L2 (no flush needed)"},
+                   "l2": f"inputs {16 * total / 1e9:.1f} GB per step > 129 MB L2 (no flush needed)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_src, "kernel": "k_bstream", "algorithmic_bytes_per_launch": 16 * total,
                      "traffic": recorded_traffic("k_bstream", total)},
