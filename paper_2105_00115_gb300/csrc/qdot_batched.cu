@@ -30,9 +30,12 @@ struct PairStats {
   int e_max;                // max block maximum u_b (kNone if none)
   int e_min;                // min component key
   int status;               // QDOT_OK, QDOT_ERR_ARG or QDOT_ERR_NONFINITE
-  int pad;
+  int f_spec;               // f if every block of the pair is non-empty (a lower bound of f)
   unsigned long long nbins; // non-empty blocks
   unsigned long long zeros; // ZERO components
+  int e_run;                // running lower bound of e_max shared by the warps (biased), for speculation
+  int pad2;
+  long long pad3;
 };
 
 struct BatchHeader {
@@ -45,6 +48,7 @@ struct BatchHeader {
 __global__ void __launch_bounds__(1024) k_bplan(const double* const* __restrict__ xs,
                                                 const double* const* __restrict__ ys,
                                                 const long long* __restrict__ ns, int count, int log2b,
+                                                double eps, int split_budget,
                                                 long long rec_capacity, long long* __restrict__ gpre,
                                                 long long* __restrict__ bpre, PairStats* __restrict__ ps,
                                                 BatchHeader* __restrict__ hdr) {
@@ -64,9 +68,12 @@ __global__ void __launch_bounds__(1024) k_bplan(const double* const* __restrict_
     s.e_max = kNone;
     s.e_min = INT_MAX;
     s.status = ok ? QDOT_OK : QDOT_ERR_ARG;
-    s.pad = 0;
+    s.f_spec = nb > 0 ? floor_log2_ratio(eps, split_budget ? (unsigned long long)nb : 1ull) : 0;
     s.nbins = 0;
     s.zeros = 0;
+    s.e_run = kNone;
+    s.pad2 = 0;
+    s.pad3 = 0;
     ps[p] = s;
   }
   s_g[t] = g;
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream(const double
                                                                   const long long* __restrict__ bpre,
                                                                   PairStats* __restrict__ ps,
                                                                   const BatchHeader* __restrict__ hdr,
-                                                                  BlockRec* __restrict__ recs) {
+                                                                  BlockRec* __restrict__ recs, int mh, int ms) {
   constexpr int L = Map<LOG2B>::L, BPI = Map<LOG2B>::BPI;
   if (hdr->status != QDOT_OK) return;
   const int lane = threadIdx.x & 31;
@@ -160,6 +167,10 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream(const double
   uint4* ring = STAGED ? s_bring + (threadIdx.x >> 5) * (2 * kStageWords) : nullptr;
   long long gg = g0;
   int p = find_pair(gpre, count, g0);
+  // speculation state of the current pair (see the one-pass kernel): e_lo is
+  // a lower bound of the pair's e_max; the first two items of the warp in a
+  // pair get every candidate
+  int e_lo = kNone, piter = 0;
   Chunk cur, nxt;
   if (STAGED) {
     issue_item<LOG2B>(xs[p], ys[p], ns[p], gg - gpre[p], lane, ring);
@@ -187,15 +198,38 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream(const double
     int M = 0, zeros = 0, u;
     int key[8];
     int cmax = kNone;
+    unsigned cands = kCandAll, top = kCandD;
     if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
       u = group_max<L>(cmax);
       M = 8;
-      acc_fast<LOG2B, kCandAll>(cur, key, u, aH, aS, aD);
+      int wmax = u;
+#pragma unroll
+      for (int o = L; o < 32; o <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+      if ((piter & 7) == 1) {  // the pair's shared bound, every 8 items
+        int seen = kNone;
+        if (lane == 0) seen = *(volatile int*)&ps[p].e_run;
+        e_lo = max(e_lo, __shfl_sync(0xffffffffu, seen, 0));
+      }
+      if (wmax > e_lo) {
+        e_lo = wmax;
+        if (lane == 0) atomicMax(&ps[p].e_run, wmax);
+      }
+      unsigned want = kCandAll;
+      if (piter >= 4) {  // windows wider than the single call's: a pair's warps see less of it
+        const int sig_hi = LOG2B + u - e_lo - ps[p].f_spec + 1;  // >= the block's score
+        want = 0;
+        if (sig_hi >= ms) want |= kCandD;
+        if (sig_hi >= mh && sig_hi - 10 < ms) want |= kCandS;
+        if (sig_hi >= 0 && sig_hi - 8 < mh) want |= kCandH;
+      }
+      cands = __reduce_or_sync(0xffffffffu, want);
+      top = cands ? (1u << (31 - __clz((int)cands))) : kCandD;
+      acc_fast_mask<LOG2B>(cands, cur, key, u, aH, aS, aD);
     } else {
       u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);
     }
     int kb, ub, mb;
-    const long long word = block_record_word<LOG2B>(aH, aS, aD, M, u, kCandAll, sub, &kb, &ub, &mb);
+    const long long word = block_record_word<LOG2B>(aH, aS, aD, M, u, cands, sub, &kb, &ub, &mb, top);
     const long long lb = (gg - gpre[p]) * BPI + g;  // block index within pair p
     const long long nblk_p = bpre[p + 1] - bpre[p];
     zeros_l += zeros;
@@ -206,7 +240,13 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream(const double
       }
       if (sub < 4) reinterpret_cast<long long*>(recs + bpre[p] + lb)[sub] = word;
     }
-    if (np != p) flush(p);
+    if (np != p) {
+      flush(p);
+      e_lo = kNone;
+      piter = 0;
+    } else {
+      ++piter;
+    }
     if (!STAGED) cur = nxt;
     gg = ngg;
     p = np;
@@ -215,7 +255,31 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream(const double
   flush(p < count ? p : count - 1);
 }
 
-__global__ void __launch_bounds__(256) k_bfinal(const long long* __restrict__ ns, const long long* __restrict__ bpre,
+constexpr int kBatchRepairQueue = 256;
+
+__device__ long long recompute_any(const double* x, const double* y, long long n, long long blk, int u, int cls,
+                                   int log2b) {
+  switch (log2b) {
+    case 5: return recompute_candidate<5>(x, y, n, blk, u, cls);
+    case 6: return recompute_candidate<6>(x, y, n, blk, u, cls);
+    case 7: return recompute_candidate<7>(x, y, n, blk, u, cls);
+    default: return recompute_candidate<8>(x, y, n, blk, u, cls);
+  }
+}
+
+__device__ long long recompute_any_warp(const double* x, const double* y, long long n, long long blk, int u, int cls,
+                                        int log2b, int lane) {
+  switch (log2b) {
+    case 5: return recompute_candidate_warp<5>(x, y, n, blk, u, cls, lane);
+    case 6: return recompute_candidate_warp<6>(x, y, n, blk, u, cls, lane);
+    case 7: return recompute_candidate_warp<7>(x, y, n, blk, u, cls, lane);
+    default: return recompute_candidate_warp<8>(x, y, n, blk, u, cls, lane);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bfinal(const double* const* __restrict__ xs,
+                                                const double* const* __restrict__ ys,
+                                                const long long* __restrict__ ns, const long long* __restrict__ bpre,
                                                 const PairStats* __restrict__ ps, const BatchHeader* __restrict__ hdr,
                                                 const BlockRec* __restrict__ recs, int log2b, qdot_params prm,
                                                 qdot_result* __restrict__ outs) {
@@ -234,6 +298,14 @@ __global__ void __launch_bounds__(256) k_bfinal(const long long* __restrict__ ns
   const int lsb = e_max - L;
   i128 acc = 0;
   unsigned long long c[4] = {0, 0, 0, 0};
+  __shared__ long long s_qblk[kBatchRepairQueue];
+  __shared__ int s_qinfo[kBatchRepairQueue];
+  __shared__ int s_nq;
+  if (threadIdx.x == 0) s_nq = 0;
+  __syncthreads();
+  const double* xp = xs[p];
+  const double* yp = ys[p];
+  const long long np_ = ns[p];
   if (status == QDOT_OK) {
     for (long long r = bpre[p] + threadIdx.x; r < bpre[p + 1]; r += blockDim.x) {
       const longlong2 r0 = reinterpret_cast<const longlong2*>(recs + r)[0];
@@ -241,11 +313,34 @@ __global__ void __launch_bounds__(256) k_bfinal(const long long* __restrict__ ns
       const int key = (int)(short)(r1.y & 0xFFFF);
       if (key == kEmptyKey) continue;
       const int u = (int)(short)((r1.y >> 16) & 0xFFFF);
-      const unsigned m = rec_count((unsigned)((unsigned long long)r1.y >> 32));
+      const unsigned mw = (unsigned)((unsigned long long)r1.y >> 32);
+      const unsigned m = rec_count(mw);
       const int cls = precision_of((long long)key - e_max - f + 1, mh, ms);
 #pragma unroll
       for (int k = 0; k < 4; ++k) c[k] += (cls == k) ? m : 0u;
-      acc += record_candidate(r0.x, r0.y, r1.x, u, cls, log2b, lsb);
+      if (cls == kPerf) continue;
+      if (rec_cands(mw) & (1u << cls)) {
+        acc += record_candidate(r0.x, r0.y, r1.x, u, cls, log2b, lsb);
+        continue;
+      }
+      const int slot = atomicAdd(&s_nq, 1);  // recomputed by the CTA's warps below
+      if (slot < kBatchRepairQueue) {
+        s_qblk[slot] = r - bpre[p];
+        s_qinfo[slot] = (u << 2) | cls;
+      } else {
+        const long long v = recompute_any(xp, yp, np_, r - bpre[p], u, cls, log2b);
+        acc += record_candidate(v, v, v, u, cls, log2b, lsb);
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nq = min(s_nq, kBatchRepairQueue);
+    for (int qi = w; qi < nq; qi += (int)(blockDim.x >> 5)) {
+      const int cls = s_qinfo[qi] & 3, u = s_qinfo[qi] >> 2;
+      const long long v = recompute_any_warp(xp, yp, np_, s_qblk[qi], u, cls, log2b, lane);
+      if (lane == 0) acc += record_candidate(v, v, v, u, cls, log2b, lsb);
     }
   }
   acc = warp_sum_i128(acc);
@@ -303,7 +398,7 @@ BatchLayout batch_layout(int count) {
 template <int LOG2B, int THREADS, bool STAGED>
 cudaError_t launch_stream(int grid, const double* const* xs, const double* const* ys, const long long* ns, int count,
                           const long long* gpre, const long long* bpre, PairStats* ps, const BatchHeader* hdr,
-                          BlockRec* recs, cudaStream_t st) {
+                          BlockRec* recs, int mh, int ms, cudaStream_t st) {
   const int smem = STAGED ? (THREADS / 32) * 2 * kStageWords * 16 : 0;
   static bool attr_set = false;  // per instantiation
   if (STAGED && !attr_set) {
@@ -312,7 +407,8 @@ cudaError_t launch_stream(int grid, const double* const* xs, const double* const
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_bstream<LOG2B, THREADS, STAGED><<<grid, THREADS, smem, st>>>(xs, ys, ns, count, gpre, bpre, ps, hdr, recs);
+  k_bstream<LOG2B, THREADS, STAGED><<<grid, THREADS, smem, st>>>(xs, ys, ns, count, gpre, bpre, ps, hdr, recs, mh,
+                                                                  ms);
   return cudaGetLastError();
 }
 
@@ -327,22 +423,23 @@ cudaError_t launch_batched_lb(const double* const* xs, const double* const* ys, 
   auto* ps = reinterpret_cast<PairStats*>(ws + l.off_ps);
   auto* recs = reinterpret_cast<BlockRec*>(ws + l.off_rec);
   const long long capacity = (long long)((ws_bytes - l.fixed) / sizeof(BlockRec));
-  k_bplan<<<1, 1024, 0, st>>>(xs, ys, ns, count, LOG2B, capacity, gpre, bpre, ps, hdr);
+  k_bplan<<<1, 1024, 0, st>>>(xs, ys, ns, count, LOG2B, p->eps, p->split_budget, capacity, gpre, bpre, ps, hdr);
   const int sms = device_info().sms > 0 ? device_info().sms : 152;
   const int grid = t.grid_ctas > 0 ? t.grid_ctas : t.ctas_per_sm * sms;
   cudaEvent_t ev0, ev1;
   kernel_events(&ev0, &ev1);
   if (ev0) cudaEventRecord(ev0, st);
   cudaError_t e;
+  const int mh = p->mant_reading ? 11 : 10, ms = p->mant_reading ? 24 : 23;
   if (t.threads_per_cta == 128)
-    e = t.staged ? launch_stream<LOG2B, 128, true>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, st)
-                 : launch_stream<LOG2B, 128, false>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, st);
+    e = t.staged ? launch_stream<LOG2B, 128, true>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, mh, ms, st)
+                 : launch_stream<LOG2B, 128, false>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, mh, ms, st);
   else
-    e = t.staged ? launch_stream<LOG2B, 256, true>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, st)
-                 : launch_stream<LOG2B, 256, false>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, st);
+    e = t.staged ? launch_stream<LOG2B, 256, true>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, mh, ms, st)
+                 : launch_stream<LOG2B, 256, false>(grid, xs, ys, ns, count, gpre, bpre, ps, hdr, recs, mh, ms, st);
   if (e != cudaSuccess) return e;
   if (ev1) cudaEventRecord(ev1, st);
-  k_bfinal<<<count, 256, 0, st>>>(ns, bpre, ps, hdr, recs, LOG2B, *p, outs);
+  k_bfinal<<<count, 256, 0, st>>>(xs, ys, ns, bpre, ps, hdr, recs, LOG2B, *p, outs);
   return cudaGetLastError();
 }
 

@@ -374,9 +374,15 @@ __device__ __forceinline__ int chunk_general(const Chunk& ch, long long& aH, lon
 template <int LOG2B>
 __device__ __forceinline__ long long block_record_word(long long aH, long long aS, double aD, int M, int u_b,
                                                       unsigned cands, int sub, int* key_out, int* u_out,
-                                                      int* m_out) {
+                                                      int* m_out, unsigned top = kCandD) {
   constexpr int L = Map<LOG2B>::L;
-  long long aDi = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
+  long long aDi = 0;
+  if (top == kCandS)  // aD holds the class `top` (see acc_fast)
+    aS = __double2ll_rz(aD * 4503599627370496.0);  // 2^52
+  else if (top == kCandH)
+    aH = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
+  else
+    aDi = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
   aH = group_sum<L>(aH);
   aS = group_sum<L>(aS);
   aDi = group_sum<L>(aDi);
