@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--workload", default="single", choices=["single", "batched", "cg", "cg_batched", "power", "backward"])
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-1e-10 summary of the single line")
     ap.add_argument("--grid", type=int, default=128, help="CG grid edge (cg workload)")
+    ap.add_argument("--cg-coef", default="variable", choices=["variable", "const"],
+                    help="cg workload: coefficients 10^U(-3,3) per cell, or all 1 (well conditioned)")
     ap.add_argument("--eps-sweep", action="store_true", help="cg workload: ACG at eps = 1e-16 .. 1e3")
     ap.add_argument("--sweep", action="store_true",
                     help="single workload: time every block in {1, 32, 256} x eps in {1e-15, 1e-8, 1e-1} on the "
@@ -310,12 +312,15 @@ def run_batched(args, rank, world, local, dist, lib):
     }
 
 
-def cg_problem(edge: int):
+def cg_problem(edge: int, coef: str = "variable"):
     import torch
 
     import paper_2105_00115_gb300 as q
     import workloads
-    rp, col, val = workloads.poisson3d(edge, edge, edge)
+    if coef == "const":
+        rp, col, val = workloads.laplace3d(edge, edge, edge)
+    else:
+        rp, col, val = workloads.poisson3d(edge, edge, edge)
     b = workloads.rhs(rp.shape[0] - 1)
     return q.Csr(rp, col, val), torch.from_numpy(b).cuda(), int(col.shape[0])
 
@@ -358,7 +363,7 @@ def cg_summary(args, edge=128):
 def run_cg(args, rank, world, local, dist, lib):
     """CG workload: one step = one ACG solve to 1e-10 (metric: seconds)."""
     import torch
-    A, bd, nnz = cg_problem(args.grid)
+    A, bd, nnz = cg_problem(args.grid, args.cg_coef)
     for _ in range(max(args.warmup, 1)):
         timed_cg(A, bd, args.eps, args.block, "qdot")
     clocks = Clocks(local, not args.no_clocks)
@@ -390,7 +395,7 @@ def run_cg(args, rank, world, local, dist, lib):
         "metric": "CG time-to-1e-10", "value": world / t_mean, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * t_mean,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"ACG (qdot dots) on the 7-point variable-coefficient Poisson {args.grid}^3 problem, "
+        "config": {"workload": f"ACG (qdot dots) on the 7-point {args.cg_coef}-coefficient Poisson {args.grid}^3 problem, "
                                f"eps={args.eps:g}, block={args.block}, relative residual 1e-10",
                    "n": n, "nnz": nnz, "l2": "matrix 190 MB > 129 MB L2 streamed every iteration"},
         "seconds_to_1e-10": t_mean, "iters": its, "status": info["status"], "true_relres": info["true_relres"],

@@ -27,10 +27,10 @@ namespace {
 using namespace chunk;
 namespace cgrp = cooperative_groups;
 
-constexpr int kFusedThreads = 256;
+constexpr int kFusedThreads = 512;
 constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kFusedItems = 8;    // items per warp at most
-constexpr int kFusedCtasPerSm = 2;
+constexpr int kFusedCtasPerSm = 1;
 
 struct FusedBlock {  // one block's candidates (in shared memory)
   long long h, s, d;

@@ -473,28 +473,23 @@ __global__ void k_bcg_finish(const BatchSys* __restrict__ sys, const qdot_result
   infos[s] = o;
 }
 
-// Plain FP64 dot per system (the comparator): per-tile partial sums, then one
+// Plain FP64 dot per system (the comparator): one warp per tile (8 rows per
+// lane, one fused multiply-add chain each), per-tile partial sums, then one
 // warp per system adds its tiles in order (deterministic).
 __global__ void k_bcg_dot_tiles(BatchView v, const double* __restrict__ a, const double* __restrict__ b,
                                 double* __restrict__ part, const long long* __restrict__ ns_dot) {
-  __shared__ double sw[kTileRows / 32];
-  for (long long t = blockIdx.x; t < v.ntiles; t += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < v.ntiles; t += nwarps) {
     const RowTile tile = v.tiles[t];
     double acc = 0.0;
-    if (ns_dot[tile.sys] > 0 && (int)threadIdx.x < tile.nrows) {
-      const long long i = padded(v, tile.sys, tile.row0 + threadIdx.x);
-      acc = a[i] * b[i];
+    if (ns_dot[tile.sys] > 0) {
+      const long long i0 = padded(v, tile.sys, tile.row0);
+      for (int r = lane; r < tile.nrows; r += 32) acc = fma(a[i0 + r], b[i0 + r], acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sum = 0.0;
-      for (int w = 0; w < kTileRows / 32; ++w) sum += sw[w];
-      part[t] = sum;
-    }
-    __syncthreads();
+    if (lane == 0) part[t] = acc;
   }
 }
 
