@@ -282,10 +282,14 @@ size_t qdot_dot_fp64_workspace_size(void);
 qdot_status qdot_dot_fp64(const double* x, const double* y, int64_t n, double* out, void* ws, size_t ws_bytes,
                           void* stream);
 
-/* End-to-end call from host buffers: copies x_host, y_host (n doubles each,
- * preferably pinned) into the caller's device buffers x_dev, y_dev, runs
- * qdot() on them, and copies the result into *out_host.  Synchronises the
- * stream before returning. */
+/* End-to-end call from host buffers x_host, y_host (n doubles each); the
+ * result lands in *out_host and the stream is synchronised before returning.
+ * Page-locked buffers that are mapped into the device's address space
+ * (cudaHostAlloc, cudaHostRegister; all of them on a unified-address system)
+ * are read in place by the kernels over the host link, in the same single
+ * pass, and x_dev, y_dev are left untouched.  Other host memory is first
+ * copied into the caller's device buffers x_dev, y_dev, in chunks over
+ * several streams. */
 qdot_status qdot_from_host(const double* x_host, const double* y_host, int64_t n, const qdot_params* p,
                            qdot_result* out_host, double* x_dev, double* y_dev, qdot_result* out_dev, void* ws,
                            size_t ws_bytes, void* stream);

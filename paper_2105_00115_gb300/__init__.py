@@ -153,7 +153,9 @@ def dot_fp64(x, y, stream=None) -> float:
 
 def from_host(x_host, y_host, eps=1e-16, block=32, split_budget=1, mant_reading=0, path="auto", x_dev=None,
               y_dev=None, ws=None, stream=None) -> QdotResult:
-    """End-to-end qdot from host tensors (pinned CPU float64): copies in, runs, copies the result out."""
+    """End-to-end qdot from CPU float64 tensors.  Pinned (page-locked) tensors
+    are read in place by the kernels over the host link; others are copied into
+    x_dev, y_dev first."""
     torch = _torch()
     lib = load()
     n = x_host.numel()

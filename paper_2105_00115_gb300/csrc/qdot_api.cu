@@ -135,6 +135,50 @@ qdot_status cuda_fail(const char* what, cudaError_t e) {
   return QDOT_ERR_CUDA;
 }
 
+// Device address of a page-locked host buffer mapped into the device's
+// address space, or NULL (pageable or unknown memory, or any error).
+const double* mapped_host_pointer(const double* h) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error state of the query
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return static_cast<const double*>(a.devicePointer);
+}
+
+// Streams and events for the host-to-device copies of qdot_from_host, one
+// set per device, created on first use and kept for the process.
+constexpr int kCopyStreams = 4;
+struct CopyStreams {
+  cudaStream_t s[kCopyStreams];
+  cudaEvent_t start, done[kCopyStreams];
+};
+
+CopyStreams* copy_streams(cudaError_t* err) {
+  static std::mutex mu;
+  static CopyStreams* sets[64] = {nullptr};
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return nullptr;
+  if (dev < 0 || dev >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!sets[dev]) {
+    auto* c = new CopyStreams();
+    for (int i = 0; i < kCopyStreams && *err == cudaSuccess; ++i) {
+      *err = cudaStreamCreateWithFlags(&c->s[i], cudaStreamNonBlocking);
+      if (*err == cudaSuccess) *err = cudaEventCreateWithFlags(&c->done[i], cudaEventDisableTiming);
+    }
+    if (*err == cudaSuccess) *err = cudaEventCreateWithFlags(&c->start, cudaEventDisableTiming);
+    if (*err != cudaSuccess) return nullptr;
+    sets[dev] = c;
+  }
+  return sets[dev];
+}
+
 }  // namespace
 
 namespace qd {
@@ -239,10 +283,43 @@ qdot_status qdot_from_host(const double* x_host, const double* y_host, int64_t n
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (n > 0) {
-    e = cudaMemcpyAsync(x_dev, x_host, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail("qdot_from_host: copy of x", e);
-    e = cudaMemcpyAsync(y_dev, y_host, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail("qdot_from_host: copy of y", e);
+    // Page-locked host buffers are read in place by the kernels, over the
+    // host link, in the same single pass (no staging copy).
+    const double* xd = mapped_host_pointer(x_host);
+    const double* yd = mapped_host_pointer(y_host);
+    if (xd && yd) {
+      qdot_status s = qdot(xd, yd, n, p, out_dev, nullptr, ws, ws_bytes, stream);
+      if (s != QDOT_OK) return s;
+      e = cudaMemcpyAsync(out_host, out_dev, sizeof(qdot_result), cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return cuda_fail("qdot_from_host: copy of the result", e);
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail("qdot_from_host: synchronize", e);
+      return QDOT_OK;
+    }
+    // Otherwise the two vectors go up in chunks spread over the library's copy streams
+    // (several copy engines in flight), ordered after the caller's stream.
+    CopyStreams* cs = copy_streams(&e);
+    if (!cs) return cuda_fail("qdot_from_host: copy streams", e);
+    if ((e = cudaEventRecord(cs->start, st)) != cudaSuccess) return cuda_fail("qdot_from_host: event", e);
+    const size_t bytes = sizeof(double) * (size_t)n;
+    const size_t chunk = std::max<size_t>(bytes / (2 * kCopyStreams), 1u << 20);
+    int k = 0;
+    for (int v = 0; v < 2; ++v) {
+      const char* src = reinterpret_cast<const char*>(v ? y_host : x_host);
+      char* dst = reinterpret_cast<char*>(v ? y_dev : x_dev);
+      for (size_t off = 0; off < bytes; off += chunk, ++k) {
+        cudaStream_t cst = cs->s[k % kCopyStreams];
+        if (k < kCopyStreams && (e = cudaStreamWaitEvent(cst, cs->start, 0)) != cudaSuccess)
+          return cuda_fail("qdot_from_host: wait", e);
+        e = cudaMemcpyAsync(dst + off, src + off, std::min(chunk, bytes - off), cudaMemcpyHostToDevice, cst);
+        if (e != cudaSuccess) return cuda_fail("qdot_from_host: copy of x / y", e);
+      }
+    }
+    for (int i = 0; i < std::min(k, kCopyStreams); ++i) {
+      if ((e = cudaEventRecord(cs->done[i], cs->s[i])) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(st, cs->done[i], 0)) != cudaSuccess)
+        return cuda_fail("qdot_from_host: join", e);
+    }
   }
   qdot_status s = qdot(x_dev, y_dev, n, p, out_dev, nullptr, ws, ws_bytes, stream);
   if (s != QDOT_OK) return s;

@@ -161,12 +161,15 @@ def test_dot_fp64_comparator(q, orc):
 def test_from_host_end_to_end(q, orc):
     import torch
     x, y = workloads.pair("b", 200001, 77)
-    xh = torch.from_numpy(x).pin_memory()
-    yh = torch.from_numpy(y).pin_memory()
     ref = orc.qdot(x, y, eps=1e-8, block=32)
-    r = q.from_host(xh, yh, eps=1e-8, block=32)
-    assert r.count == tuple(ref.count)
-    assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
+    # pinned host memory (read in place) and pageable host memory (copied)
+    for xh, yh in ((torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()),
+                   (torch.from_numpy(x.copy()), torch.from_numpy(y.copy()))):
+        for block in (32, 1):
+            r = q.from_host(xh, yh, eps=1e-8, block=block)
+            ref_b = ref if block == 32 else orc.qdot(x, y, eps=1e-8, block=1)
+            assert r.count == tuple(ref_b.count)
+            assert abs(r.value - ref_b.value) <= TOL * orc.abs_dot_exact(x, y)
 
 
 def _repairs(q, x, y, eps, block):
