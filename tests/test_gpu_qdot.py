@@ -1,6 +1,6 @@
 """GPU parity of qdot (C ABI through the Python binding) against the CPU oracle.
 
-Bar (spec tolerance): class map, quantized values, class counts, e_max,
+Bar: class map, quantized values, class counts, e_max,
 e_min, N_bins and f bit-exact; z within 1e-13 * sum_i |x_i y_i| (the exact
 sum of absolute products, from the oracle).
 """
