@@ -265,3 +265,24 @@ def test_full_size_lognormal(q, orc, block):
     assert r.count == tuple(ref.count)
     assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
     assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
+
+
+@pytest.mark.parametrize("kind,ts", [("A", (10, 40, 100)), ("B", (2, 10, 30))])
+def test_paper_distributions_within_bound(q, orc, kind, ts):
+    """The paper's synthetic arrays (s 2^p, s ~ U[0.5, 1), p uniform or
+    normal with parameter t): the GPU value's error against the exact dot stays
+    within the a-priori bound N_bins 2^(e_max + f) (plus the GPU's summation
+    tolerance), and the class counts match the oracle's."""
+    for n in (100, 1000, 10**4, 10**5):
+        for t in ts:
+            xd = workloads.exponent_dist(kind, n, t, 900 + n + t)
+            yd = workloads.exponent_dist(kind, n, t, 950 + n + t)
+            x, y = xd.cpu().numpy(), yd.cpu().numpy()
+            exact = orc.dot_exact(x, y)
+            for eps in (1e-16, 1e-8, 1e-3):
+                for block in (0, 1, 32):
+                    r = q.qdot(xd, yd, eps=eps, block=block)
+                    ref = orc.qdot(x, y, eps=eps, block=block)
+                    assert r.count == tuple(ref.count)
+                    assert abs(r.value - exact) <= r.bound + TOL * orc.abs_dot_exact(x, y)
+                    assert r.bound <= eps * 2.0 ** r.e_max  # N_bins 2^f <= eps

@@ -190,3 +190,19 @@ def batched_cg_systems(count: int = 256, lo: int = 16, hi: int = 64, seed: int =
     edges = rng.integers(lo, hi + 1, count)
     blocks = [poisson3d(int(e), int(e), int(e), seed=seed + 1 + i) for i, e in enumerate(edges)]
     return (*block_diagonal(blocks), edges)
+
+
+def exponent_dist(kind: str, n: int, t: float, seed: int, device="cuda"):
+    """The paper's synthetic arrays (Sec. 6.1): components s * 2^p with
+    s ~ U[0.5, 1) and p ~ U[-t/2, t/2] (kind 'A') or p ~ N(0, t/2) (kind 'B'),
+    drawn on `device` from a seeded torch generator; float64."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    s = torch.rand(n, generator=g, device=device, dtype=torch.float64) * 0.5 + 0.5
+    if kind == "A":
+        p = (torch.rand(n, generator=g, device=device, dtype=torch.float64) - 0.5) * t
+    elif kind == "B":
+        p = torch.randn(n, generator=g, device=device, dtype=torch.float64) * (0.5 * t)
+    else:
+        raise ValueError(kind)
+    return s * torch.exp2(p)
