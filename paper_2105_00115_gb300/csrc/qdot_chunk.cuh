@@ -312,6 +312,80 @@ __device__ __forceinline__ void acc_fast_mask(unsigned mask, const Chunk& ch, co
   }
 }
 
+// Per-lane variant of acc_fast for the single-call stream: each lane's block
+// has its own primary class `prim` (its highest wanted candidate), computed on
+// the FP64 pipe with that lane's rounding: SINGLE lanes round both operands to
+// 24 bits, HALF lanes to 11 bits, DOUBLE lanes (and lanes with no candidate)
+// keep them.  RMODE (warp-uniform) has bit 0 set when some lane is SINGLE,
+// bit 1 when some lane is HALF.  The SINGLE rounding uses per-lane constants
+// that leave the other lanes' operands unchanged; the HALF rounding is a
+// branch (HALF lanes are usually few, next to perforated ones).  IMASK (warp-uniform) names
+// the secondary classes some block wants besides its primary; they take the
+// integer path in every lane, and each block keeps only its own.
+template <int LOG2B, int RMODE, unsigned IMASK>
+__device__ __forceinline__ void acc_lane(const Chunk& ch, const int (&key)[8], int u, unsigned prim, long long& aH,
+                                         long long& aS, double& aF) {
+  constexpr int K = LOG2B;
+  const bool rs = prim == kCandS, rh = prim == kCandH;
+  // SINGLE: round to nearest even at bit 29 of the 64-bit pattern
+  const uint32_t s_inc = rs ? 0x0FFFFFFFu : 0u;    // half an ulp less one
+  const uint32_t s_bit = rs ? 1u : 0u;             // picks the lsb (ties to even)
+  const uint32_t s_mask = rs ? 0xE0000000u : ~0u;  // clears the bits below the cut
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t hx = (uint32_t)(ch.x[j] >> 32), lx = (uint32_t)ch.x[j];
+    const uint32_t hy = (uint32_t)(ch.y[j] >> 32), ly = (uint32_t)ch.y[j];
+    const int d = u - key[j];
+    if (IMASK) {
+      const uint32_t mx = (hx & 0xFFFFFu) | 0x100000u, my = (hy & 0xFFFFFu) | 0x100000u;
+      const int sgn = product_sign(hx, hy);
+      if (IMASK & kCandH) {
+        const int yh = (int)half_sig(my, ly) * sgn;
+        aH += sar64((long long)((int)half_sig(mx, lx) * yh) << (40 - K), d);
+      }
+      if (IMASK & kCandS) {
+        const int ys = (int)single_sig(my, ly) * (sgn * 64);
+        aS += sar64((long long)(int)single_sig(mx, lx) * (long long)ys, d);
+      }
+    }
+    const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
+    uint64_t xo = ((uint64_t)((hx & 0x800FFFFFu) | 0x3FF00000u) << 32) | lx;
+    uint64_t yo = ((uint64_t)((hy & 0x800FFFFFu) | ye) << 32) | ly;
+    if (RMODE & 1) {  // a carry out of the fraction moves into the exponent field
+      xo = (xo + (s_inc + (((uint32_t)xo >> 29) & s_bit))) & (0xFFFFFFFF00000000ull | s_mask);
+      yo = (yo + (s_inc + (((uint32_t)yo >> 29) & s_bit))) & (0xFFFFFFFF00000000ull | s_mask);
+    }
+    if ((RMODE & 2) && rh) {  // HALF lanes: round at bit 42
+      xo = round_bits<42>(xo);
+      yo = round_bits<42>(yo);
+    }
+    aF = fma(__longlong_as_double((long long)xo), __longlong_as_double((long long)yo), aF);
+  }
+}
+
+template <int LOG2B, int RMODE>
+__device__ __forceinline__ void acc_lane_i(unsigned imask, const Chunk& ch, const int (&key)[8], int u, unsigned prim,
+                                           long long& aH, long long& aS, double& aF) {
+  switch (imask >> 1) {  // warp-uniform
+    case 0: acc_lane<LOG2B, RMODE, 0u>(ch, key, u, prim, aH, aS, aF); break;
+    case 1: acc_lane<LOG2B, RMODE, kCandH>(ch, key, u, prim, aH, aS, aF); break;
+    case 2: acc_lane<LOG2B, RMODE, kCandS>(ch, key, u, prim, aH, aS, aF); break;
+    default: acc_lane<LOG2B, RMODE, kCandH | kCandS>(ch, key, u, prim, aH, aS, aF); break;
+  }
+}
+
+// rounds: the primaries of the warp's lanes (OR); imask: their secondaries (OR).
+template <int LOG2B>
+__device__ __forceinline__ void acc_lane_mask(unsigned rounds, unsigned imask, const Chunk& ch, const int (&key)[8],
+                                              int u, unsigned prim, long long& aH, long long& aS, double& aF) {
+  switch (((rounds & kCandS) ? 1 : 0) | ((rounds & kCandH) ? 2 : 0)) {  // warp-uniform
+    case 0: acc_lane_i<LOG2B, 0>(imask, ch, key, u, prim, aH, aS, aF); break;
+    case 1: acc_lane_i<LOG2B, 1>(imask, ch, key, u, prim, aH, aS, aF); break;
+    case 2: acc_lane_i<LOG2B, 2>(imask, ch, key, u, prim, aH, aS, aF); break;
+    default: acc_lane_i<LOG2B, 3>(imask, ch, key, u, prim, aH, aS, aF); break;
+  }
+}
+
 // Candidates of one component with key e (biased) in a block with maximum
 // key u (biased), any finite nonzero x, y given by their bits.
 template <int LOG2B>
@@ -409,27 +483,43 @@ __device__ __forceinline__ long long block_record_word(long long aH, long long a
 // u_b = s_b - ceil(log2 M_b).
 constexpr int kMetaKeyBias = 4096;
 
-// aF holds the candidate of class `top` (kCand*): D or H on the grid
-// 2^(u - 60 + K), S on 2^(u - 52).
+// Blocks of up to kSumAllLanes lanes sum every class unconditionally (two
+// shuffle steps cost less than the branch around them).
+constexpr int kSumAllLanes = 4;
+
+// aF holds the candidate of class `top` (kCand*, per lane; 0 for a block
+// with no candidate): D or H on the grid 2^(u - 60 + K), S on 2^(u - 52).
+// `sumset` (warp-uniform) names the classes
+// any block of the warp keeps: only those are summed over the block's lanes.
+// `full` (warp-uniform): every lane holds 8 nonzero components, so M_b = B.
 template <int LOG2B>
 __device__ __forceinline__ void block_record_compact(long long aH, long long aS, double aF, unsigned top, int M,
-                                                     int u_b, unsigned stored, int sub, int* key_out, int* u_out,
-                                                     int* m_out, long long* slot, unsigned* meta,
-                                                     long long* half_out) {
+                                                     int u_b, unsigned stored, unsigned sumset, bool full, int sub,
+                                                     int* key_out, int* u_out, int* m_out, long long* slot,
+                                                     unsigned* meta, long long* half_out) {
   constexpr int L = Map<LOG2B>::L;
   long long aDi = 0;
-  if (top == kCandS)
-    aS = __double2ll_rz(aF * 4503599627370496.0);  // 2^52
-  else if (top == kCandH)
-    aH = __double2ll_rz(aF * (double)(1ll << (60 - LOG2B)));
-  else
-    aDi = __double2ll_rz(aF * (double)(1ll << (60 - LOG2B)));
-  aH = group_sum<L>(aH);
-  aS = group_sum<L>(aS);
-  aDi = group_sum<L>(aDi);
-  M = group_sum_i<L>(M);
+  {  // aF onto its class's grid; `top` may differ between lanes
+    const long long v = __double2ll_rz(aF * (top == kCandS ? 4503599627370496.0 : (double)(1ll << (60 - LOG2B))));
+    if (top == kCandS)
+      aS = v;
+    else if (top == kCandH)
+      aH = v;
+    else
+      aDi = v;
+  }
+  if (L <= kSumAllLanes || (sumset & kCandH)) aH = group_sum<L>(aH);
+  if (L <= kSumAllLanes || (sumset & kCandS)) aS = group_sum<L>(aS);
+  if (L <= kSumAllLanes || (sumset & kCandD)) aDi = group_sum<L>(aDi);
+  int key;
   const int u = u_b - 2046;
-  const int key = M > 0 ? ceil_log2_u32((uint32_t)M) + u : (int)kEmptyKey;
+  if (full) {
+    M = 1 << LOG2B;
+    key = LOG2B + u;
+  } else {
+    M = group_sum_i<L>(M);
+    key = M > 0 ? ceil_log2_u32((uint32_t)M) + u : (int)kEmptyKey;
+  }
   *key_out = key;
   *u_out = u;
   *m_out = M;

@@ -66,20 +66,27 @@ struct OpPart {
 
 // Speculation windows: a block gets the SINGLE candidate when its score may
 // lie up to kWinS below its upper bound sigma_hi, the HALF candidate up to
-// kWinH below (HALF blocks are rare at practical eps, so its window is
-// narrow).  During the first 1/16 of a warp's items, while the running bound
-// of e_max still climbs fast, both windows widen by kWinEarly; a warp's first
-// two items get every candidate.
-constexpr int kWinS = 6, kWinH = 5, kWinEarly = 8;
+// kWinH below.  For a block of B nonzero components the score is sigma_hi
+// less (e_max - e_lo) less (f - f_spec); once the running bound e_lo has
+// caught up with e_max, and unless many blocks are empty (f > f_spec), that
+// difference is 0, so each block gets one candidate: the class of sigma_hi.
+// During the first 1/kEarlyDiv of a warp's items, while the bound still
+// climbs, both windows widen by kWinEarly, and a warp's first two items get
+// every candidate.  A block whose class falls outside its window is
+// recomputed by the gather.
+constexpr int kWinS = 0, kWinH = 0, kWinEarly = 8, kEarlyDiv = 32;
+// The warps share their bounds of e_max through one word: each raises it
+// when it sees a larger key and reads it every kExchange items, using each
+// read kExchange items later (the first read, at item 1, at item 2).
+constexpr int kExchange = 4;
 
 // Blocks a gather CTA can queue for recomputation by its warps together.
 constexpr int kRepairQueue = 512;
 
 // The candidates a block with maximum key u (biased; kNone if empty) should
 // get, after folding u into the warp's running bound e_lo of e_max.  e_lo
-// also takes in erun, the bound shared by all warps: read at item 1 (used at
-// item 2), then every 16 items, each read used 16 items later so that it
-// completes while other items run.
+// also takes in erun, the bound shared by all warps, on the schedule above;
+// each read has a few items' time to complete before its value is used.
 template <int LOG2B>
 __device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter, long long early_items, int f_spec,
                                                       int mh, int ms, int* erun, int& e_lo, int& pending) {
@@ -87,8 +94,8 @@ __device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter,
   int wmax = u;
 #pragma unroll
   for (int o = L; o < 32; o <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-  if ((iter & 15) == 1) {
-    const int seen = __shfl_sync(0xffffffffu, pending, 0);  // loaded 16 items ago (none at the first read)
+  if ((iter & (kExchange - 1)) == 1) {
+    const int seen = __shfl_sync(0xffffffffu, pending, 0);  // loaded kExchange items ago (none at the first read)
     if (lane == 0) pending = *(volatile int*)erun;
     e_lo = max(e_lo, seen);
   }
@@ -133,7 +140,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
   int pending = kNone;  // lane 0: the value erun held at its last read
   int iter = 0;
   const long long my_items = gwarp < nitems ? (nitems - gwarp + nwarps - 1) / nwarps : 0;
-  const long long early_items = (my_items + 15) / 16;
+  const long long early_items = (my_items + kEarlyDiv - 1) / kEarlyDiv;
   extern __shared__ uint4 s_ring[];
   uint4* ring = s_ring + (threadIdx.x >> 5) * (kStages * kStageWords);
   // prologue: items it, it + nwarps, ... (kStages - 1 of them) in flight
@@ -159,16 +166,20 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
     long long aH = 0, aS = 0;
     double aD = 0.0;
     int M = 0, zeros = 0, u;
-    unsigned want = 0, top = kCandD;  // top: the class aD holds (the general path computes D there)
+    unsigned want = 0, top = kCandD;  // top: the class aD holds, per lane (the general path computes D there)
+    unsigned sumset = kCandAll;        // the classes summed into the block records
     int key[8];
     int cmax = kNone;
-    if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
+    const bool plain = __all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin));
+    if (plain) {
       u = group_max<L>(cmax);
       M = 8;
       want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
-      const unsigned cands = __reduce_or_sync(0xffffffffu, want);
-      top = cands ? (1u << (31 - __clz((int)cands))) : kCandD;
-      acc_fast_mask<LOG2B>(cands, cur, key, u, aH, aS, aD);
+      top = want ? (1u << (31 - __clz((int)want))) : 0u;  // the block's primary class
+      const unsigned both = __reduce_or_sync(0xffffffffu, top | (want & ~top) << 4);
+      const unsigned rounds = both & 0xFu, imask = both >> 4;
+      sumset = rounds | imask;
+      acc_lane_mask<LOG2B>(rounds, imask, cur, key, u, top, aH, aS, aD);
     } else {
       u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);  // every candidate
       want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
     int kb, ub, mb;
     long long slot, half;
     unsigned meta;
-    block_record_compact<LOG2B>(aH, aS, aD, top, M, u, want, sub, &kb, &ub, &mb, &slot, &meta, &half);
+    block_record_compact<LOG2B>(aH, aS, aD, top, M, u, want, sumset, plain, sub, &kb, &ub, &mb, &slot, &meta, &half);
     const long long blk = it * BPI + g;
     zeros_l += zeros;
     if (blk < nblocks) {
