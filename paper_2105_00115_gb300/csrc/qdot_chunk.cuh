@@ -483,43 +483,27 @@ __device__ __forceinline__ long long block_record_word(long long aH, long long a
 // u_b = s_b - ceil(log2 M_b).
 constexpr int kMetaKeyBias = 4096;
 
-// Blocks of up to kSumAllLanes lanes sum every class unconditionally (two
-// shuffle steps cost less than the branch around them).
-constexpr int kSumAllLanes = 4;
-
-// aF holds the candidate of class `top` (kCand*, per lane; 0 for a block
-// with no candidate): D or H on the grid 2^(u - 60 + K), S on 2^(u - 52).
-// `sumset` (warp-uniform) names the classes
-// any block of the warp keeps: only those are summed over the block's lanes.
-// `full` (warp-uniform): every lane holds 8 nonzero components, so M_b = B.
+// aF holds the candidate of class `top` (kCand*): D or H on the grid
+// 2^(u - 60 + K), S on 2^(u - 52).
 template <int LOG2B>
 __device__ __forceinline__ void block_record_compact(long long aH, long long aS, double aF, unsigned top, int M,
-                                                     int u_b, unsigned stored, unsigned sumset, bool full, int sub,
-                                                     int* key_out, int* u_out, int* m_out, long long* slot,
-                                                     unsigned* meta, long long* half_out) {
+                                                     int u_b, unsigned stored, int sub, int* key_out, int* u_out,
+                                                     int* m_out, long long* slot, unsigned* meta,
+                                                     long long* half_out) {
   constexpr int L = Map<LOG2B>::L;
   long long aDi = 0;
-  {  // aF onto its class's grid; `top` may differ between lanes
-    const long long v = __double2ll_rz(aF * (top == kCandS ? 4503599627370496.0 : (double)(1ll << (60 - LOG2B))));
-    if (top == kCandS)
-      aS = v;
-    else if (top == kCandH)
-      aH = v;
-    else
-      aDi = v;
-  }
-  if (L <= kSumAllLanes || (sumset & kCandH)) aH = group_sum<L>(aH);
-  if (L <= kSumAllLanes || (sumset & kCandS)) aS = group_sum<L>(aS);
-  if (L <= kSumAllLanes || (sumset & kCandD)) aDi = group_sum<L>(aDi);
-  int key;
+  if (top == kCandS)
+    aS = __double2ll_rz(aF * 4503599627370496.0);  // 2^52
+  else if (top == kCandH)
+    aH = __double2ll_rz(aF * (double)(1ll << (60 - LOG2B)));
+  else
+    aDi = __double2ll_rz(aF * (double)(1ll << (60 - LOG2B)));
+  aH = group_sum<L>(aH);
+  aS = group_sum<L>(aS);
+  aDi = group_sum<L>(aDi);
+  M = group_sum_i<L>(M);
   const int u = u_b - 2046;
-  if (full) {
-    M = 1 << LOG2B;
-    key = LOG2B + u;
-  } else {
-    M = group_sum_i<L>(M);
-    key = M > 0 ? ceil_log2_u32((uint32_t)M) + u : (int)kEmptyKey;
-  }
+  const int key = M > 0 ? ceil_log2_u32((uint32_t)M) + u : (int)kEmptyKey;
   *key_out = key;
   *u_out = u;
   *m_out = M;
@@ -537,6 +521,29 @@ __device__ __forceinline__ void block_record_compact(long long aH, long long aS,
   }
   *slot = sub == 0 ? hi : lo;
   *meta = M > 0 ? ((unsigned)(key + kMetaKeyBias) | ((unsigned)M << 13) | ((stored >> 1) << 22)) : 0u;
+}
+
+// Compact record of a plain block (B nonzero components, M_b = B): every lane
+// of the block holds the same primary class `prim` in aF, so one group sum
+// covers it; the secondaries (classes in `imask`, warp-uniform) are summed
+// only when some block of the warp keeps one.
+template <int LOG2B>
+__device__ __forceinline__ void block_record_plain(long long aH, long long aS, double aF, unsigned prim,
+                                                   unsigned imask, int u_b, unsigned stored, int sub, int* u_out,
+                                                   long long* slot, unsigned* meta, long long* half_out) {
+  constexpr int L = Map<LOG2B>::L;
+  const long long hi =
+      group_sum<L>(__double2ll_rz(aF * (prim == kCandS ? 4503599627370496.0 : (double)(1ll << (60 - LOG2B)))));
+  long long lo = 0, h = 0;
+  if (imask & kCandH) h = group_sum<L>(aH);
+  if (imask & kCandS) aS = group_sum<L>(aS);
+  if (stored & ~prim & kCandS) lo = aS;
+  else if (stored & ~prim & kCandH) lo = h;
+  const int u = u_b - 2046;
+  *u_out = u;
+  *half_out = h;
+  *slot = sub == 0 ? hi : lo;
+  *meta = (unsigned)(LOG2B + u + kMetaKeyBias) | ((unsigned)(1 << LOG2B) << 13) | ((stored >> 1) << 22);
 }
 
 __device__ __forceinline__ void unpack_meta(unsigned meta, int* key, int* u, unsigned* m, unsigned* stored) {

@@ -59,7 +59,7 @@ struct OnePassPlan {
   int window = 0;         // keys kept per record
   long long units = 0;    // work units (each produces one record)
   long long unit_blocks = 0;
-  size_t off_sel = 0, off_hdr = 0, off_rec = 0, off_misc = 0, off_meta = 0, off_slot3 = 0;
+  size_t off_sel = 0, off_hdr = 0, off_rec = 0, off_misc = 0, off_slot1 = 0, off_meta = 0, off_slot3 = 0;
   size_t rec_bytes = 0;
   size_t total = 0;
 };

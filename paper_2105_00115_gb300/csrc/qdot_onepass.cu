@@ -56,6 +56,7 @@ struct OpHeader {
   int status;
   int erun;            // running lower bound of e_max shared by the streaming warps (biased)
   long long zeros;
+  unsigned done;       // gather CTAs that have written their partial (zeroed by k_op_select)
 };
 struct OpPart {
   i128 sum;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
                                                            int mh, int ms, int* __restrict__ erun,
                                                            WarpStats* __restrict__ wstats,
                                                            long long* __restrict__ slots,
+                                                           long long* __restrict__ slots1,
                                                            unsigned* __restrict__ metas,
                                                            long long* __restrict__ slot3) {
   constexpr int L = Map<LOG2B>::L, BPI = Map<LOG2B>::BPI;
@@ -166,29 +168,28 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
     long long aH = 0, aS = 0;
     double aD = 0.0;
     int M = 0, zeros = 0, u;
-    unsigned want = 0, top = kCandD;  // top: the class aD holds, per lane (the general path computes D there)
-    unsigned sumset = kCandAll;        // the classes summed into the block records
+    unsigned want = 0;
     int key[8];
     int cmax = kNone;
-    const bool plain = __all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin));
-    if (plain) {
+    int ub, mb;
+    long long slot, half;
+    unsigned meta;
+    if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
       u = group_max<L>(cmax);
-      M = 8;
       want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
-      top = want ? (1u << (31 - __clz((int)want))) : 0u;  // the block's primary class
-      const unsigned both = __reduce_or_sync(0xffffffffu, top | (want & ~top) << 4);
+      const unsigned prim = want ? (1u << (31 - __clz((int)want))) : 0u;  // the block's primary class
+      const unsigned both = __reduce_or_sync(0xffffffffu, prim | (want & ~prim) << 4);
       const unsigned rounds = both & 0xFu, imask = both >> 4;
-      sumset = rounds | imask;
-      acc_lane_mask<LOG2B>(rounds, imask, cur, key, u, top, aH, aS, aD);
+      acc_lane_mask<LOG2B>(rounds, imask, cur, key, u, prim, aH, aS, aD);
+      block_record_plain<LOG2B>(aH, aS, aD, prim, imask, u, want, sub, &ub, &slot, &meta, &half);
+      mb = 1 << LOG2B;
     } else {
       u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);  // every candidate
       want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
+      int kb;
+      block_record_compact<LOG2B>(aH, aS, aD, kCandD, M, u, want, sub, &kb, &ub, &mb, &slot, &meta, &half);
     }
     // the record keeps the block's wanted candidates
-    int kb, ub, mb;
-    long long slot, half;
-    unsigned meta;
-    block_record_compact<LOG2B>(aH, aS, aD, top, M, u, want, sumset, plain, sub, &kb, &ub, &mb, &slot, &meta, &half);
     const long long blk = it * BPI + g;
     zeros_l += zeros;
     if (blk < nblocks) {
@@ -196,8 +197,11 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
         nbins += (sub == 0);
         emax_l = max(emax_l, ub);
       }
-      if (sub < 2) slots[2 * blk + sub] = slot;
-      if (sub == 2) metas[blk] = meta;
+      if (sub == 0) {
+        slots[blk] = slot;
+        metas[blk] = meta;
+      }
+      if (sub == 1 && (want & (want - 1u)) != 0u) slots1[blk] = slot;  // the next one, if kept
       if (sub == 3 && want == kCandAll && blk < 2 * nwarps * BPI) slot3[blk] = half;  // first two items only
     }
     it += nwarps;
@@ -283,6 +287,7 @@ __global__ void __launch_bounds__(1024) k_op_select(const WarpStats* __restrict_
     hdr->lsb = emax - hdr->L;
     hdr->status = status;
     hdr->zeros = z;
+    hdr->done = 0u;
   }
   __syncthreads();
   const int e_max = sel->e_max, f = s_f;
@@ -294,21 +299,23 @@ __global__ void __launch_bounds__(1024) k_op_select(const WarpStats* __restrict_
 // Deferred selection: per block record pick the candidate of the block's
 // class and add it exactly to a fixed-point sum anchored at 2^(e_max - L).
 // A candidate the streaming kernel skipped is recomputed here from x and y.
+// The last CTA to finish adds the CTA partials in order and writes the result.
 template <int LOG2B>
-__global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__ slots,
+__global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restrict__ slots,
+                                                   const long long* __restrict__ slots1,
                                                    const unsigned* __restrict__ metas,
                                                    const long long* __restrict__ slot3, long long n_early,
-                                                   long long nblocks,
-                                                   const qdot_selection* __restrict__ sel,
-                                                   const OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
+                                                   long long nblocks, qdot_selection* __restrict__ sel,
+                                                   OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
                                                    const double* __restrict__ x, const double* __restrict__ y,
-                                                   long long n) {
+                                                   long long n, qdot_result* __restrict__ out) {
   __shared__ uint8_t s_lut[kKeyCount];
   __shared__ i128 s_sum[8];
   __shared__ unsigned long long s_cnt[8][5];
   __shared__ long long s_qblk[kRepairQueue];  // blocks to recompute ...
   __shared__ int s_qinfo[kRepairQueue];       // ... with u << 2 | class
   __shared__ int s_nqueue;
+  __shared__ bool s_last;
   for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
     reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
   if (threadIdx.x == 0) s_nqueue = 0;
@@ -317,59 +324,52 @@ __global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__
   const bool ok = hdr->status == QDOT_OK;
   i128 acc = 0;
   unsigned long long c[5] = {0, 0, 0, 0, 0};  // per class, then recomputed blocks
-  // four consecutive blocks per thread and step: one 16-byte load of their
-  // meta words, then the (independent) loads of the chosen candidates
-  const long long nquads = (nblocks + 3) >> 2;
-  for (long long qd4 = (long long)blockIdx.x * blockDim.x + threadIdx.x; ok && qd4 < nquads;
-       qd4 += (long long)gridDim.x * blockDim.x) {
-    const long long b0 = qd4 << 2;
-    unsigned mw[4];
-    if (b0 + 4 <= nblocks) {
-      const uint4 m4 = reinterpret_cast<const uint4*>(metas)[qd4];
-      mw[0] = m4.x;
-      mw[1] = m4.y;
-      mw[2] = m4.z;
-      mw[3] = m4.w;
+  // one block: its meta word and its first candidate slot
+  auto take = [&](unsigned mw, long long sl0, long long blk) {
+    if (mw == 0) return;  // empty block
+    int key, u;
+    unsigned m, stored;
+    unpack_meta(mw, &key, &u, &m, &stored);
+    const int cls = s_lut[key - kKeyMin];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) c[j] += (cls == j) ? m : 0u;
+    if (cls == kPerf) return;
+    if (stored == kCandAll && cls == kHalf && blk >= n_early) stored = 0;  // never written
+    long long v;
+    if (stored & (1u << cls)) {
+      const int top = 31 - __clz((int)stored);  // the highest stored class sits in slot 0
+      v = (stored == kCandAll && cls == kHalf) ? slot3[blk]  // blk < n_early by construction
+                                               : (cls == top ? sl0 : slots1[blk]);
     } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) mw[k] = b0 + k < nblocks ? metas[b0 + k] : 0u;
-    }
-    long long v[4];
-    int uu[4], cl[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      cl[k] = kPerf;
-      uu[k] = 0;
-      v[k] = 0;
-      if (mw[k] == 0) continue;  // empty block
-      int key;
-      unsigned m, stored;
-      unpack_meta(mw[k], &key, &uu[k], &m, &stored);
-      const int cls = s_lut[key - kKeyMin];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) c[j] += (cls == j) ? m : 0u;
-      if (cls == kPerf) continue;
-      cl[k] = cls;
-      if (stored == kCandAll && cls == kHalf && b0 + k >= n_early) stored = 0;  // never written
-      if (stored & (1u << cls)) {
-        const int top = 31 - __clz((int)stored);  // the highest stored class sits in slot 0
-        v[k] = (stored == kCandAll && cls == kHalf) ? slot3[b0 + k]  // b0 + k < n_early by construction
-                                                    : slots[2 * (b0 + k) + (cls == top ? 0 : 1)];
-      } else {
-        ++c[4];
-        const int slot = atomicAdd(&s_nqueue, 1);
-        if (slot < kRepairQueue) {  // the CTA's warps recompute it together after the sweep
-          s_qblk[slot] = b0 + k;
-          s_qinfo[slot] = (uu[k] << 2) | cls;
-          cl[k] = kPerf;
-        } else {  // queue full: this thread recomputes it alone
-          v[k] = recompute_candidate<LOG2B>(x, y, n, b0 + k, uu[k], cls);
-        }
+      ++c[4];
+      const int q = atomicAdd(&s_nqueue, 1);
+      if (q < kRepairQueue) {  // the CTA's warps recompute it together after the sweep
+        s_qblk[q] = blk;
+        s_qinfo[q] = (u << 2) | cls;
+        return;
       }
+      v = recompute_candidate<LOG2B>(x, y, n, blk, u, cls);  // queue full: this thread alone
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (cl[k] != kPerf) acc += candidate_to_fixed(v[k], cl[k], uu[k], LOG2B, lsb);
+    acc += candidate_to_fixed(v, cls, u, LOG2B, lsb);
+  };
+  // four consecutive blocks per quad: their meta words (16 bytes) and first
+  // slots (32 bytes) are independent loads; a second slot is read only for
+  // a block whose class is its second kept candidate
+  const long long nquads = nblocks >> 2;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const uint4* m4 = reinterpret_cast<const uint4*>(metas);
+  const longlong2* s4 = reinterpret_cast<const longlong2*>(slots);
+  for (long long qa = (long long)blockIdx.x * blockDim.x + threadIdx.x; ok && qa < nquads; qa += stride) {
+    const uint4 ma = m4[qa];
+    const longlong2 sa = s4[2 * qa], sb = s4[2 * qa + 1];
+    take(ma.x, sa.x, 4 * qa);
+    take(ma.y, sa.y, 4 * qa + 1);
+    take(ma.z, sb.x, 4 * qa + 2);
+    take(ma.w, sb.y, 4 * qa + 3);
+  }
+  {  // the last nblocks % 4 blocks
+    const long long blk = 4 * nquads + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ok && blk < nblocks) take(metas[blk], slots[blk], blk);
   }
   // queued recomputations: one warp per block, lanes striding over its
   // components (coalesced), partial candidates summed over the warp
@@ -400,24 +400,26 @@ __global__ void __launch_bounds__(256) k_op_gather(const long long* __restrict__
       p.repairs += s_cnt[i][4];
     }
     parts[blockIdx.x] = p;
+    __threadfence();  // the partial is visible before the arrival is counted
+    s_last = atomicAdd(&hdr->done, 1u) == gridDim.x - 1;
   }
-}
-
-__global__ void __launch_bounds__(256) k_op_final(const OpPart* __restrict__ parts, int np,
-                                                  qdot_selection* __restrict__ sel,
-                                                  const OpHeader* __restrict__ hdr, qdot_result* __restrict__ out) {
-  __shared__ i128 s_sum[8];
-  __shared__ unsigned long long s_cnt[8][5];
-  i128 acc = 0;
-  unsigned long long c[5] = {0, 0, 0, 0, 0};
+  __syncthreads();
+  if (!s_last) return;
+  // last CTA: the exact sum of the partials, in CTA order, then one rounding
+  __threadfence();
+  const int np = gridDim.x;
+  acc = 0;
+  for (int k = 0; k < 5; ++k) c[k] = 0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    acc += parts[i].sum;
-    for (int k = 0; k < 4; ++k) c[k] += parts[i].cnt[k];
-    c[4] += parts[i].repairs;
+    const unsigned long long* pw = reinterpret_cast<const unsigned long long*>(parts + i);
+    const unsigned long long lo = __ldcg(pw), hi = __ldcg(pw + 1);
+    acc += (i128)(((unsigned __int128)hi << 64) | lo);
+    for (int k = 0; k < 4; ++k) c[k] += __ldcg(&parts[i].cnt[k]);
+    c[4] += __ldcg(&parts[i].repairs);
   }
   acc = warp_sum_i128(acc);
   for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // s_sum, s_cnt are reused
   if (lane == 0) {
     s_sum[w] = acc;
     for (int k = 0; k < 5; ++k) s_cnt[w][k] = c[k];
@@ -465,6 +467,7 @@ cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_pa
   auto* hdr = reinterpret_cast<OpHeader*>(ws + pl.off_hdr);
   auto* wst = reinterpret_cast<WarpStats*>(ws + pl.off_rec);
   auto* slots = reinterpret_cast<long long*>(ws + pl.off_misc);
+  auto* slots1 = reinterpret_cast<long long*>(ws + pl.off_slot1);
   auto* metas = reinterpret_cast<unsigned*>(ws + pl.off_meta);
   auto* slot3 = reinterpret_cast<long long*>(ws + pl.off_slot3);
   auto* parts = reinterpret_cast<OpPart*>(ws + pl.off_sel + align_up(sizeof(qdot_selection), 256) +
@@ -484,14 +487,14 @@ cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_pa
     if (e != cudaSuccess) return e;
     smem_set = true;
   }
-  k_onepass<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, slots, metas, slot3);
+  k_onepass<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, slots, slots1,
+                                                          metas, slot3);
   if (ev1) cudaEventRecord(ev1, st);
   const int nw = pl.grid * kOpWarps;
   k_op_select<<<1, 1024, 0, st>>>(wst, nw, n, *p, sel, hdr);
   const int gather_grid = 4 * (device_info().sms > 0 ? device_info().sms : 152);
-  k_op_gather<LOG2B><<<gather_grid, 256, 0, st>>>(slots, metas, slot3, 2ll * pl.grid * kOpWarps * Map<LOG2B>::BPI,
-                                                    nblocks, sel, hdr, parts, x, y, n);
-  k_op_final<<<1, 256, 0, st>>>(parts, gather_grid, sel, hdr, out);
+  k_op_gather<LOG2B><<<gather_grid, 256, 0, st>>>(slots, slots1, metas, slot3, 2ll * pl.grid * kOpWarps * Map<LOG2B>::BPI,
+                                                    nblocks, sel, hdr, parts, x, y, n, out);
   return cudaGetLastError();
 }
 
@@ -519,8 +522,10 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
   off = align_up(off + sizeof(OpPart) * 4 * sms, 256);  // gather partials
   pl.off_rec = off;
   off = align_up(off + sizeof(WarpStats) * pl.grid * kOpWarps, 256);
-  pl.off_misc = off;  // two candidate slots per block
-  off = align_up(off + 2 * sizeof(long long) * (size_t)nblocks, 256);
+  pl.off_misc = off;  // the first candidate slot of every block
+  off = align_up(off + sizeof(long long) * (size_t)nblocks, 256);
+  pl.off_slot1 = off;  // the second, written for blocks that keep two or more
+  off = align_up(off + sizeof(long long) * (size_t)nblocks, 256);
   pl.off_meta = off;  // one meta word per block
   off = align_up(off + sizeof(unsigned) * (size_t)nblocks, 256);
   pl.off_slot3 = off;  // HALF candidates of the blocks of every warp's first two items
