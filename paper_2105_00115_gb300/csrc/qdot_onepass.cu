@@ -76,6 +76,10 @@ struct OpPart {
 // every candidate.  A block whose class falls outside its window is
 // recomputed by the gather.
 constexpr int kWinS = 0, kWinH = 0, kWinEarly = 8, kEarlyDiv = 32;
+// The windows also stay wide until the warp's bound e_lo has held for kCalm
+// items: while it still rises (short vectors, heavy tails) it may be short
+// of e_max by more than a window of 0 allows.
+constexpr int kCalm = 8;
 // The warps share their bounds of e_max through one word: each raises it
 // when it sees a larger key and reads it every kExchange items, using each
 // read kExchange items later (the first read, at item 1, at item 2).
@@ -90,7 +94,8 @@ constexpr int kRepairQueue = 512;
 // each read has a few items' time to complete before its value is used.
 template <int LOG2B>
 __device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter, long long early_items, int f_spec,
-                                                      int mh, int ms, int* erun, int& e_lo, int& pending) {
+                                                      int mh, int ms, int* erun, int& e_lo, int& pending,
+                                                      int& raised) {
   constexpr int L = Map<LOG2B>::L;
   int wmax = u;
 #pragma unroll
@@ -98,11 +103,21 @@ __device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter,
   if ((iter & (kExchange - 1)) == 1) {
     const int seen = __shfl_sync(0xffffffffu, pending, 0);  // loaded kExchange items ago (none at the first read)
     if (lane == 0) pending = *(volatile int*)erun;
-    e_lo = max(e_lo, seen);
+    if (seen > e_lo) {
+      e_lo = seen;
+      raised = iter;
+    }
   }
-  if (iter == 2) e_lo = max(e_lo, __shfl_sync(0xffffffffu, pending, 0));  // the read issued at item 1
+  if (iter == 2) {  // the read issued at item 1
+    const int seen = __shfl_sync(0xffffffffu, pending, 0);
+    if (seen > e_lo) {
+      e_lo = seen;
+      raised = iter;
+    }
+  }
   if (wmax > e_lo) {
     e_lo = wmax;
+    raised = iter;
     if (lane == 0) atomicMax(erun, wmax);
   }
   if (u == kNone) return 0;
@@ -110,7 +125,7 @@ __device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter,
   // sigma_hi >= the block's score (e_lo <= e_max, f_spec <= f, ceil(log2 M_b) <= log2 B);
   // candidates for the classes of scores in the window below sigma_hi
   const int sig_hi = LOG2B + u - e_lo - f_spec + 1;
-  const int wide = iter < early_items ? kWinEarly : 0;
+  const int wide = (iter < early_items || iter - raised < kCalm) ? kWinEarly : 0;
   unsigned want = 0;
   if (sig_hi >= ms) want |= kCandD;
   if (sig_hi >= mh && sig_hi - kWinS - wide < ms) want |= kCandS;
@@ -140,6 +155,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
 
   int e_lo = kNone;     // lower bound of e_max (biased), the same in every lane
   int pending = kNone;  // lane 0: the value erun held at its last read
+  int raised = 0;       // the item at which e_lo last rose
   int iter = 0;
   const long long my_items = gwarp < nitems ? (nitems - gwarp + nwarps - 1) / nwarps : 0;
   const long long early_items = (my_items + kEarlyDiv - 1) / kEarlyDiv;
@@ -176,7 +192,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
     unsigned meta;
     if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
       u = group_max<L>(cmax);
-      want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
+      want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending, raised);
       const unsigned prim = want ? (1u << (31 - __clz((int)want))) : 0u;  // the block's primary class
       const unsigned both = __reduce_or_sync(0xffffffffu, prim | (want & ~prim) << 4);
       const unsigned rounds = both & 0xFu, imask = both >> 4;
@@ -185,7 +201,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
       mb = 1 << LOG2B;
     } else {
       u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);  // every candidate
-      want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending);
+      want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending, raised);
       int kb;
       block_record_compact<LOG2B>(aH, aS, aD, kCandD, M, u, want, sub, &kb, &ub, &mb, &slot, &meta, &half);
     }
