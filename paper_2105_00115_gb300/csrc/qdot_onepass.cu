@@ -79,11 +79,11 @@ constexpr int kWinS = 0, kWinH = 0, kWinEarly = 8, kEarlyDiv = 32;
 // The windows also stay wide until the warp's bound e_lo has held for kCalm
 // items: while it still rises (short vectors, heavy tails) it may be short
 // of e_max by more than a window of 0 allows.
-constexpr int kCalm = 8;
+constexpr int kCalm = 4;
 // The warps share their bounds of e_max through one word: each raises it
 // when it sees a larger key and reads it every kExchange items, using each
 // read kExchange items later (the first read, at item 1, at item 2).
-constexpr int kExchange = 4;
+constexpr int kExchange = 2;
 
 // Blocks a gather CTA can queue for recomputation by its warps together.
 constexpr int kRepairQueue = 512;
