@@ -520,7 +520,7 @@ bool one_pass_supported(int64_t n, const qdot_params* p, bool aligned16) {
   return aligned16 && n > 0 && p->block >= 32 && p->block <= 256;
 }
 
-int one_pass_launches(int64_t, const qdot_params*) { return 4; }
+int one_pass_launches(int64_t, const qdot_params*) { return 3; }  // stream, select, gather
 
 OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
   OnePassPlan pl;
