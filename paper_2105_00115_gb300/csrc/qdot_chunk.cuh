@@ -476,7 +476,8 @@ __device__ __forceinline__ long long block_record_word(long long aH, long long a
 
 // Compact record of one block (single-call path): two candidate slots and a
 // 32-bit meta word
-//   meta = (s_b + kMetaKeyBias) | M_b << 13 | (stored >> 1) << 22,  0 = empty block,
+//   meta = (s_b + kMetaKeyBias) | M_b << 13 | (stored >> 1) << 22 | ceil(log2 M_b) << 25,
+//   0 = empty block,
 // where `stored` (kCand* bits) names the candidates kept: the higher class in
 // slot 0, the next in slot 1; when all three are kept (a warp's first items)
 // the HALF candidate goes to a third, short array indexed by block.
@@ -520,7 +521,9 @@ __device__ __forceinline__ void block_record_compact(long long aH, long long aS,
     lo = 0;
   }
   *slot = sub == 0 ? hi : lo;
-  *meta = M > 0 ? ((unsigned)(key + kMetaKeyBias) | ((unsigned)M << 13) | ((stored >> 1) << 22)) : 0u;
+  *meta = M > 0 ? ((unsigned)(key + kMetaKeyBias) | ((unsigned)M << 13) | ((stored >> 1) << 22) |
+                    ((unsigned)(key - u) << 25))
+                 : 0u;
 }
 
 // Compact record of a plain block (B nonzero components, M_b = B): every lane
@@ -543,14 +546,15 @@ __device__ __forceinline__ void block_record_plain(long long aH, long long aS, d
   *u_out = u;
   *half_out = h;
   *slot = sub == 0 ? hi : lo;
-  *meta = (unsigned)(LOG2B + u + kMetaKeyBias) | ((unsigned)(1 << LOG2B) << 13) | ((stored >> 1) << 22);
+  *meta = (unsigned)(LOG2B + u + kMetaKeyBias) | ((unsigned)(1 << LOG2B) << 13) | ((stored >> 1) << 22) |
+          ((unsigned)LOG2B << 25);
 }
 
 __device__ __forceinline__ void unpack_meta(unsigned meta, int* key, int* u, unsigned* m, unsigned* stored) {
   *key = (int)(meta & 0x1FFFu) - kMetaKeyBias;
   *m = (meta >> 13) & 0x1FFu;
   *stored = ((meta >> 22) & 7u) << 1;
-  *u = *key - ceil_log2_u32(*m);
+  *u = *key - (int)((meta >> 25) & 0xFu);
 }
 
 // A block candidate of class cls on its grid, moved to the fixed-point grid

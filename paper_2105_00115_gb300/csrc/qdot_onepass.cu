@@ -338,35 +338,48 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
   __syncthreads();
   const int lsb = hdr->lsb;
   const bool ok = hdr->status == QDOT_OK;
-  i128 acc = 0;
-  unsigned long long c[5] = {0, 0, 0, 0, 0};  // per class, then recomputed blocks
+  i128 acc = 0;                               // recomputed candidates
+  unsigned long long acc_lo = 0;              // the others: a 128-bit sum in two words
+  long long acc_hi = 0;
+  unsigned long long c_ph = 0, c_sd = 0;      // components per class, two 32-bit counts per word
+  unsigned long long c_rep = 0;               // recomputed blocks
   // one block: its meta word and its first candidate slot
   auto take = [&](unsigned mw, long long sl0, long long blk) {
-    if (mw == 0) return;  // empty block
     int key, u;
     unsigned m, stored;
-    unpack_meta(mw, &key, &u, &m, &stored);
-    const int cls = s_lut[key - kKeyMin];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) c[j] += (cls == j) ? m : 0u;
-    if (cls == kPerf) return;
-    if (stored == kCandAll && cls == kHalf && blk >= n_early) stored = 0;  // never written
-    long long v;
-    if (stored & (1u << cls)) {
-      const int top = 31 - __clz((int)stored);  // the highest stored class sits in slot 0
-      v = (stored == kCandAll && cls == kHalf) ? slot3[blk]  // blk < n_early by construction
-                                               : (cls == top ? sl0 : slots1[blk]);
-    } else {
-      ++c[4];
-      const int q = atomicAdd(&s_nqueue, 1);
-      if (q < kRepairQueue) {  // the CTA's warps recompute it together after the sweep
-        s_qblk[q] = blk;
-        s_qinfo[q] = (u << 2) | cls;
-        return;
+    unpack_meta(mw, &key, &u, &m, &stored);    // m = 0 for an empty block (mw = 0)
+    const int cls = mw ? (int)s_lut[mw ? key - kKeyMin : 0] : kPerf;
+    const unsigned long long cm = (unsigned long long)m << ((cls & 1) << 5);
+    if (cls < 2) c_ph += cm; else c_sd += cm;
+    const int top = 31 - __clz((int)(stored | 1u));  // the highest kept class sits in slot 0
+    long long v = sl0;
+    bool keep = cls != kPerf;
+    if (keep && cls != top) {  // a second kept candidate, or a missing one
+      if (stored == kCandAll && cls == kHalf && blk >= n_early) stored = 0;  // never written
+      if (stored & (1u << cls)) {
+        v = (stored == kCandAll && cls == kHalf) ? slot3[blk]  // blk < n_early by construction
+                                                 : slots1[blk];
+      } else {
+        ++c_rep;
+        keep = false;
+        const int q = atomicAdd(&s_nqueue, 1);
+        if (q < kRepairQueue) {  // the CTA's warps recompute it together after the sweep
+          s_qblk[q] = blk;
+          s_qinfo[q] = (u << 2) | cls;
+        } else {  // queue full: this thread recomputes it alone
+          acc += candidate_to_fixed(recompute_candidate<LOG2B>(x, y, n, blk, u, cls), cls, u, LOG2B, lsb);
+        }
       }
-      v = recompute_candidate<LOG2B>(x, y, n, blk, u, cls);  // queue full: this thread alone
     }
-    acc += candidate_to_fixed(v, cls, u, LOG2B, lsb);
+    // v on its grid 2^g, moved to 2^lsb: g - lsb <= L - 52 <= 52 (u <= e_max, L <= 104);
+    // a negative shift truncates, as the fixed-point sum does
+    const int sh = candidate_grid(cls, u, LOG2B) - lsb;
+    const int sl = min(max(sh, 0), 63), sr = min(max(-sh, 0), 63);
+    const long long w = keep ? (v >> sr) : 0ll;
+    const unsigned long long lo = (unsigned long long)w << sl;
+    const long long hi = (w >> 1) >> (63 - sl);  // the bits shifted out of lo, sign-extended
+    acc_lo += lo;
+    acc_hi += hi + (acc_lo < lo ? 1 : 0);
   };
   // four consecutive blocks per quad: their meta words (16 bytes) and first
   // slots (32 bytes) are independent loads; a second slot is read only for
@@ -398,6 +411,8 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
     const long long v = recompute_candidate_warp<LOG2B>(x, y, n, blk, u, cls, lane);
     if (lane == 0) acc += candidate_to_fixed(v, cls, u, LOG2B, lsb);
   }
+  acc += (i128)(((unsigned __int128)(unsigned long long)acc_hi << 64) | acc_lo);
+  unsigned long long c[5] = {c_ph & 0xFFFFFFFFull, c_ph >> 32, c_sd & 0xFFFFFFFFull, c_sd >> 32, c_rep};
   acc = warp_sum_i128(acc);
   for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
   if (lane == 0) {
