@@ -87,10 +87,18 @@ namespace {
 
 enum PathChoice { kTwoPass, kOnePass, kFused };
 
+// Smallest n for which QDOT_PATH_AUTO takes the one-pass path with blocks of
+// one component.
+constexpr int64_t kOnePassMinN1 = 1ll << 24;
+
 PathChoice choose_path(int64_t n, const qdot_params* p, bool al16) {
   if (p->path == QDOT_PATH_TWO_PASS) return kTwoPass;
-  const bool one = one_pass_supported(n, p, al16);
+  bool one = one_pass_supported(n, p, al16);
   if (p->path == QDOT_PATH_ONE_PASS) return one ? kOnePass : kTwoPass;
+  // blocks of one component: one pass only where a warp has enough items
+  // for its bound of e_max to settle early (otherwise most items are read
+  // twice anyway)
+  if (p->block == 1 && n < kOnePassMinN1) one = false;
   const bool fused = fused_supported(n, p, al16);
   if (p->path == QDOT_PATH_FUSED) return fused ? kFused : (one ? kOnePass : kTwoPass);
   return fused ? kFused : (one ? kOnePass : kTwoPass);

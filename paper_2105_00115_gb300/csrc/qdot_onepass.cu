@@ -1,28 +1,34 @@
-// One-pass qdot with deferred selection, blocked binning, 32 <= B <= 256.
+// One-pass qdot with deferred selection: blocked binning (32 <= B <= 256)
+// and blocks of one component (B = 1).
 //
 // The class of a block depends on the global e_max and N_bins (eq.
 // bin-score-def), which are only known after every component has been read.
-// One read of x and y is still enough: for every block b the streaming kernel
-// forms the three candidate sums the block can need,
+// One read of x and y is still enough.
+//
+// 32 <= B <= 256.  For every block b the streaming kernel forms the candidate
+// sums the block may need, of the form
 //     H_b = sum q_half(x_i) q_half(y_i),  S_b = sum q_single(x_i) q_single(y_i),
 //     D_b = sum x_i y_i,
-// exactly (fixed point below the block maximum u_b) and writes them, with the
-// block key s_b = ceil(log2 M_b) + u_b, as a 32-byte record.  Selection is
-// deferred: once e_max and N_bins are known, a gather kernel reads the records
-// (6.25% of the input bytes for B = 32, 0.8% for B = 256), takes for each
-// block the candidate of the class eq. (precision-def) assigns to
-// sigma_b = s_b - e_max - f + 1, and sums exactly.
+// on a fixed-point grid below the block maximum u_b, and writes a record: an
+// 8-byte slot per kept candidate and a 4-byte meta word with the block key
+// s_b = ceil(log2 M_b) + u_b.  Which candidates a block keeps is speculated
+// from a running lower bound of e_max (one, after the first items).  Once e_max
+// and N_bins are known, a gather kernel takes for each block the candidate of
+// the class eq. (precision-def) assigns to sigma_b = s_b - e_max - f + 1 and
+// sums exactly; a candidate the speculation skipped is recomputed from x, y.
 //
-// Mapping: a warp handles 8 blocks at a time, 4 lanes per block; per chunk of
-// 32 components of a block each lane loads 4 x 16 bytes of x and of y, and the
-// next chunk is loaded while the current one is processed.  Candidate values
-// are formed at the scale 2^(e_i - 60) and shifted right by (u - e_i) + K,
-// K = log2 B, so 64-bit block sums stay below 2^62 and are exact up to one
-// unit of 2^(u - 60 + K) per component (relative error <= B^2 2^-60 per
-// block, 2^-44 for B = 256).  The double candidate is accumulated on the FP64
-// pipe with one fused multiply-add per component on exponent-rescaled
-// operands (relative error <= (B/4) 2^-53 per lane), then converted to the
-// same grid.
+// B = 1.  Each warp item of 256 components is summed on the grid 2^(u - 52)
+// of its own largest key u, every component quantized to the class it gets if
+// the warp's bound of e_max were exact; the record keeps that bound, and the
+// gather accepts the item when it was exact and recomputes it otherwise.
+//
+// Mapping: a warp streams items of 256 components (8 per lane) through a
+// shared-memory ring with cp.async; a block spans B/8 lanes.  Candidates are
+// formed at the scale of the block maximum, so 64-bit block sums stay below
+// 2^62 and are exact up to one unit of the grid per component (relative
+// error <= B 2^-52 of the block's sum of |x_i y_i|).  The primary candidate
+// of a block goes through the FP64 pipe, one fused multiply-add per
+// component on exponent-rescaled, class-rounded operands.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -92,14 +98,11 @@ constexpr int kRepairQueue = 512;
 // get, after folding u into the warp's running bound e_lo of e_max.  e_lo
 // also takes in erun, the bound shared by all warps, on the schedule above;
 // each read has a few items' time to complete before its value is used.
-template <int LOG2B>
-__device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter, long long early_items, int f_spec,
-                                                      int mh, int ms, int* erun, int& e_lo, int& pending,
-                                                      int& raised) {
-  constexpr int L = Map<LOG2B>::L;
-  int wmax = u;
-#pragma unroll
-  for (int o = L; o < 32; o <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+// Fold the warp's largest key of this item, wmax (biased), and the shared
+// word erun into the warp's bound e_lo; `raised` records the item of its
+// last rise.
+__device__ __forceinline__ void track_bound(int wmax, int lane, int iter, int* erun, int& e_lo, int& pending,
+                                            int& raised) {
   if ((iter & (kExchange - 1)) == 1) {
     const int seen = __shfl_sync(0xffffffffu, pending, 0);  // loaded kExchange items ago (none at the first read)
     if (lane == 0) pending = *(volatile int*)erun;
@@ -120,6 +123,17 @@ __device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter,
     raised = iter;
     if (lane == 0) atomicMax(erun, wmax);
   }
+}
+
+template <int LOG2B>
+__device__ __forceinline__ unsigned candidates_wanted(int u, int lane, int iter, long long early_items, int f_spec,
+                                                      int mh, int ms, int* erun, int& e_lo, int& pending,
+                                                      int& raised) {
+  constexpr int L = Map<LOG2B>::L;
+  int wmax = u;
+#pragma unroll
+  for (int o = L; o < 32; o <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  track_bound(wmax, lane, iter, erun, e_lo, pending, raised);
   if (u == kNone) return 0;
   if (iter < 2) return kCandAll;  // before the first exchange e_lo is this warp's alone
   // sigma_hi >= the block's score (e_lo <= e_max, f_spec <= f, ceil(log2 M_b) <= log2 B);
@@ -312,6 +326,95 @@ __global__ void __launch_bounds__(1024) k_op_select(const WarpStats* __restrict_
     sel->cls[k] = (uint8_t)precision_of((long long)kKeyMin + k - e_max - f + 1, mh, ms);
 }
 
+// The end of a gather kernel: this thread's partial sum acc and counts c
+// (components per class, recomputed blocks) are summed over the CTA and
+// published; the last CTA to arrive adds all partials in CTA order and writes
+// the result, rounding once.
+__device__ __noinline__ void finish_gather(i128 acc, unsigned long long (&c)[5], OpPart* __restrict__ parts,
+                              OpHeader* __restrict__ hdr, qdot_selection* __restrict__ sel,
+                              qdot_result* __restrict__ out) {
+  __shared__ i128 s_sum[8];
+  __shared__ unsigned long long s_cnt[8][5];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  acc = warp_sum_i128(acc);
+  #pragma unroll
+  for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
+  if (lane == 0) {
+    s_sum[w] = acc;
+    #pragma unroll
+    for (int k = 0; k < 5; ++k) s_cnt[w][k] = c[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    OpPart p;
+    p.sum = 0;
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) p.cnt[k] = 0;
+    p.repairs = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      p.sum += s_sum[i];
+      #pragma unroll
+      for (int k = 0; k < 4; ++k) p.cnt[k] += s_cnt[i][k];
+      p.repairs += s_cnt[i][4];
+    }
+    parts[blockIdx.x] = p;
+    __threadfence();  // the partial is visible before the arrival is counted
+    s_last = atomicAdd(&hdr->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // last CTA: the exact sum of the partials, in CTA order, then one rounding
+  __threadfence();
+  const int np = gridDim.x;
+  acc = 0;
+  #pragma unroll
+  for (int k = 0; k < 5; ++k) c[k] = 0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    const unsigned long long* pw = reinterpret_cast<const unsigned long long*>(parts + i);
+    const unsigned long long lo = __ldcg(pw), hi = __ldcg(pw + 1);
+    acc += (i128)(((unsigned __int128)hi << 64) | lo);
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] += __ldcg(&parts[i].cnt[k]);
+    c[4] += __ldcg(&parts[i].repairs);
+  }
+  acc = warp_sum_i128(acc);
+  #pragma unroll
+  for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
+  __syncthreads();  // s_sum, s_cnt are reused
+  if (lane == 0) {
+    s_sum[w] = acc;
+    #pragma unroll
+    for (int k = 0; k < 5; ++k) s_cnt[w][k] = c[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      acc += s_sum[i];
+      #pragma unroll
+      for (int k = 0; k < 5; ++k) c[k] += s_cnt[i][k];
+    }
+    sel->reserved[0] = (int32_t)(c[4] < 0x7FFFFFFFull ? c[4] : 0x7FFFFFFFull);
+    qdot_result r;
+    r.status = hdr->status;
+    r.n_bins = sel->n_bins;
+    r.e_max = sel->e_max;
+    r.e_min = sel->e_min;
+    r.f = sel->f;
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) r.count[k] = (int64_t)c[k];
+    r.count[4] = hdr->zeros;
+    if (r.status != QDOT_OK) {
+      r.value = __longlong_as_double(0x7FF8000000000000ll);
+      r.bound = r.value;
+    } else {
+      r.value = fixed_to_double(acc, hdr->lsb);
+      r.bound = r.n_bins > 0 ? fixed_to_double((i128)r.n_bins, r.e_max + r.f) : 0.0;
+    }
+    *out = r;
+  }
+}
+
 // Deferred selection: per block record pick the candidate of the block's
 // class and add it exactly to a fixed-point sum anchored at 2^(e_max - L).
 // A candidate the streaming kernel skipped is recomputed here from x and y.
@@ -325,13 +428,10 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
                                                    OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
                                                    const double* __restrict__ x, const double* __restrict__ y,
                                                    long long n, qdot_result* __restrict__ out) {
-  __shared__ uint8_t s_lut[kKeyCount];
-  __shared__ i128 s_sum[8];
-  __shared__ unsigned long long s_cnt[8][5];
+  __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
   __shared__ long long s_qblk[kRepairQueue];  // blocks to recompute ...
   __shared__ int s_qinfo[kRepairQueue];       // ... with u << 2 | class
   __shared__ int s_nqueue;
-  __shared__ bool s_last;
   for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
     reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
   if (threadIdx.x == 0) s_nqueue = 0;
@@ -413,72 +513,281 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
   }
   acc += (i128)(((unsigned __int128)(unsigned long long)acc_hi << 64) | acc_lo);
   unsigned long long c[5] = {c_ph & 0xFFFFFFFFull, c_ph >> 32, c_sd & 0xFFFFFFFFull, c_sd >> 32, c_rep};
-  acc = warp_sum_i128(acc);
-  for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
+  finish_gather(acc, c, parts, hdr, sel, out);
+}
+
+// ---------------------------------------------------------------------------
+// Blocks of one component (B = 1).
+// ---------------------------------------------------------------------------
+
+// Item record for B = 1: the item's sum on the grid 2^(u - 52) (u its
+// largest key) and a meta word
+//   u_biased | e_lo_biased << 12 | n_half << 24 | n_single << 33 | n_double << 42,
+// bit 63 set when the gather must recompute the item (zeros, subnormals,
+// non-finite values or the vectors' end inside it).
+constexpr unsigned long long kItemRecompute = 1ull << 63;
+
+// Quantized products of a lane's 8 components into aF (FP64, relative to
+// 2^u), each with its own class cls[j] (kPerf .. kDouble).  RMODE
+// (warp-uniform): bit 0 some component is SINGLE, bit 1 some is HALF, bit 2
+// some is perforated.
+template <int RMODE>
+__device__ __forceinline__ void acc_components(const Chunk& ch, const int (&key)[8], int u, const int (&cls)[8],
+                                               double& aF) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t hx = (uint32_t)(ch.x[j] >> 32), lx = (uint32_t)ch.x[j];
+    const uint32_t hy = (uint32_t)(ch.y[j] >> 32), ly = (uint32_t)ch.y[j];
+    const int d = u - key[j];
+    const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
+    uint64_t xo = ((uint64_t)((hx & 0x800FFFFFu) | 0x3FF00000u) << 32) | lx;
+    uint64_t yo = ((uint64_t)((hy & 0x800FFFFFu) | ye) << 32) | ly;
+    if (RMODE & 1) {  // SINGLE components: round to nearest even at bit 29
+      const bool rs = cls[j] == kSingle;
+      const uint32_t inc = rs ? 0x0FFFFFFFu : 0u, bit = rs ? 1u : 0u, mask = rs ? 0xE0000000u : ~0u;
+      xo = (xo + (inc + (((uint32_t)xo >> 29) & bit))) & (0xFFFFFFFF00000000ull | mask);
+      yo = (yo + (inc + (((uint32_t)yo >> 29) & bit))) & (0xFFFFFFFF00000000ull | mask);
+    }
+    if ((RMODE & 2) && cls[j] == kHalf) {
+      xo = round_bits<42>(xo);
+      yo = round_bits<42>(yo);
+    }
+    if ((RMODE & 4) && cls[j] == kPerf) xo = 0ull;
+    aF = fma(__longlong_as_double((long long)xo), __longlong_as_double((long long)yo), aF);
+  }
+}
+
+__device__ __forceinline__ void acc_components_mode(unsigned rmode, const Chunk& ch, const int (&key)[8], int u,
+                                                    const int (&cls)[8], double& aF) {
+  switch (rmode) {  // warp-uniform
+    case 0: acc_components<0>(ch, key, u, cls, aF); break;
+    case 1: acc_components<1>(ch, key, u, cls, aF); break;
+    case 2: acc_components<2>(ch, key, u, cls, aF); break;
+    case 3: acc_components<3>(ch, key, u, cls, aF); break;
+    case 4: acc_components<4>(ch, key, u, cls, aF); break;
+    case 5: acc_components<5>(ch, key, u, cls, aF); break;
+    case 6: acc_components<6>(ch, key, u, cls, aF); break;
+    default: acc_components<7>(ch, key, u, cls, aF); break;
+  }
+}
+
+// Streaming kernel for B = 1: every component is quantized to the class of
+// its score key - e_lo - f_spec + 1, which is its true score if the warp's
+// bound e_lo equals e_max and f equals f_spec (N_bins = n, no zeros).
+__global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_c(const double* __restrict__ x,
+                                                             const double* __restrict__ y, long long n, int f_spec,
+                                                             int mh, int ms, int* __restrict__ erun,
+                                                             WarpStats* __restrict__ wstats,
+                                                             long long* __restrict__ isum,
+                                                             unsigned long long* __restrict__ imeta) {
+  constexpr int LOG2B = 8;  // the item layout of blocks of 256
+  const int lane = threadIdx.x & 31;
+  long long nbins = 0, zeros_l = 0;
+  int emax_l = kNone, kmin = INT_MAX, bad = 0;
+  const long long nitems = (n + kItem - 1) / kItem;
+  const long long gwarp = ((long long)blockIdx.x * kOpThreads + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * kOpThreads) >> 5;
+  int e_lo = kNone, pending = kNone, raised = 0, iter = 0;
+  extern __shared__ uint4 s_ring[];
+  uint4* ring = s_ring + (threadIdx.x >> 5) * (kStages * kStageWords);
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    const long long item = gwarp + st * nwarps;
+    if (item < nitems) issue_item<LOG2B>(x, y, n, item, lane, ring + st * kStageWords);
+    cp_async_commit();
+  }
+  int stage = 0;
+  long long it = gwarp;
+  Chunk cur;
+  while (it < nitems) {
+    {
+      const long long ahead = it + (long long)(kStages - 1) * nwarps;
+      const int st = stage == 0 ? kStages - 1 : stage - 1;
+      if (ahead < nitems) issue_item<LOG2B>(x, y, n, ahead, lane, ring + st * kStageWords);
+      cp_async_commit();
+    }
+    cp_async_wait<kStages - 1>();
+    read_item<LOG2B>(ring + stage * kStageWords, n, it, lane, cur);
+    stage = stage == kStages - 1 ? 0 : stage + 1;
+    int key[8];
+    int cmax = kNone;
+    long long slot = 0;
+    unsigned long long meta = kItemRecompute;
+    if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
+      const int u = __reduce_max_sync(0xffffffffu, cmax);  // the item's largest key (biased)
+      track_bound(u, lane, iter, erun, e_lo, pending, raised);
+      const int a = e_lo + f_spec - 1;  // score = key - a
+      int cls[8];
+      unsigned seen = 0, cnt = 0;  // classes present; per-class counts in 8-bit fields
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int sg = key[j] - a;
+        cls[j] = sg < 0 ? kPerf : (sg < mh ? kHalf : (sg < ms ? kSingle : kDouble));
+        seen |= 1u << cls[j];
+        cnt += 1u << (cls[j] << 3);
+      }
+      seen = __reduce_or_sync(0xffffffffu, seen);
+      const unsigned rmode = ((seen >> kSingle) & 1u) | (((seen >> kHalf) & 1u) << 1) | ((seen & 1u) << 2);
+      double aF = 0.0;
+      acc_components_mode(rmode, cur, key, u, cls, aF);
+      long long v = __double2ll_rz(aF * 4503599627370496.0);  // onto the grid 2^(u - 52)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const unsigned ps = __reduce_add_sync(0xffffffffu, cnt & 0x00FF00FFu);         // PERF, SINGLE
+      const unsigned hd = __reduce_add_sync(0xffffffffu, (cnt >> 8) & 0x00FF00FFu);  // HALF, DOUBLE
+      slot = v;
+      meta = (unsigned long long)u | ((unsigned long long)e_lo << 12) | ((unsigned long long)(hd & 0xFFFFu) << 24) |
+             ((unsigned long long)(ps >> 16) << 33) | ((unsigned long long)(hd >> 16) << 42);
+      nbins += 8;
+      emax_l = max(emax_l, u - 2046);
+    } else {  // statistics only; the gather recomputes the item
+      int wmax = kNone;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint64_t a = cur.x[j], b = cur.y[j];
+        const bool in = (cur.vmask >> j) & 1u;
+        const bool fin = !(is_nonfinite(a) || is_nonfinite(b));
+        bad |= in && !fin;
+        const bool z = is_zero(a) || is_zero(b);
+        zeros_l += in && fin && z;
+        if (in && fin && !z) {
+          const int k = exponent_of(a) + exponent_of(b) + 2046;
+          ++nbins;
+          kmin = min(kmin, k);
+          wmax = max(wmax, k);
+        }
+      }
+      wmax = __reduce_max_sync(0xffffffffu, wmax);
+      track_bound(wmax, lane, iter, erun, e_lo, pending, raised);
+      if (wmax != kNone) emax_l = max(emax_l, wmax - 2046);
+    }
+    if (lane == 0) {
+      isum[it] = slot;
+      imeta[it] = meta;
+    }
+    it += nwarps;
+    ++iter;
+  }
+  cp_async_wait<0>();
+  emax_l = __reduce_max_sync(0xffffffffu, emax_l);
+  kmin = __reduce_min_sync(0xffffffffu, kmin);
+  bad = (int)__reduce_or_sync(0xffffffffu, (unsigned)bad);
+  nbins = (long long)warp_sum_u64((unsigned long long)nbins);
+  zeros_l = (long long)warp_sum_u64((unsigned long long)zeros_l);
   if (lane == 0) {
-    s_sum[w] = acc;
-    for (int k = 0; k < 5; ++k) s_cnt[w][k] = c[k];
+    WarpStats st;
+    st.e_max = emax_l;
+    st.e_min = kmin == INT_MAX ? INT_MAX : kmin - 2046;
+    st.nonfinite = bad;
+    st.pad = 0;
+    st.nbins = nbins;
+    st.zeros = zeros_l;
+    wstats[gwarp] = st;
   }
+}
+
+// One item recomputed by a warp with the final classes: lane l takes the
+// components item*256 + l + 32k (coalesced).  Returns the item's sum on the
+// grid 2^(u - 52) (u its largest key, unbiased, in *u_out; kNone if the item
+// has no nonzero component) and adds the lane's class counts to c.
+__device__ long long recompute_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                    long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
+                                    unsigned long long (&c)[5]) {
+  uint64_t xa[8], ya[8];
+  int e[8];
+  int u = kNone;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const long long i = item * kItem + lane + 32 * k;
+    xa[k] = i < n ? (uint64_t)__double_as_longlong(x[i]) : 0ull;
+    ya[k] = i < n ? (uint64_t)__double_as_longlong(y[i]) : 0ull;
+    const bool use = !(is_zero(xa[k]) || is_zero(ya[k]) || is_nonfinite(xa[k]) || is_nonfinite(ya[k]));
+    e[k] = use ? exponent_of(xa[k]) + exponent_of(ya[k]) : kNone;
+    u = max(u, e[k]);
+  }
+  u = __reduce_max_sync(0xffffffffu, u);
+  *u_out = u;
+  if (u == kNone) return 0;
+  long long aH = 0, aS = 0;
+  double aD = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (e[k] == kNone) continue;
+    const int cls = lut[e[k] - kKeyMin];
+    c[cls] += 1;
+    if (cls != kPerf) component_candidates<8>(xa[k], ya[k], e[k] + 2046, u + 2046, 1u << cls, aH, aS, aD);
+  }
+  long long v = aH + aS + __double2ll_rz(aD * 4503599627370496.0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Gather for B = 1: an item whose bound e_lo was e_max, and f_spec f, adds
+// its record; any other item is recomputed with the final classes.  The CTA
+// takes 256 items at a time, one per thread, and its warps recompute the
+// rejected ones of each round together.  Items are dealt to the CTAs in turn
+// (item i to CTA i mod grid): the rejected items are mostly every warp's
+// first few, at the start of the vectors, and this spreads them evenly.
+__global__ void __launch_bounds__(256, 2) k_op_gather_c(const long long* __restrict__ isum,
+                                                     const unsigned long long* __restrict__ imeta, long long nitems,
+                                                     int f_spec, qdot_selection* __restrict__ sel,
+                                                     OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
+                                                     const double* __restrict__ x, const double* __restrict__ y,
+                                                     long long n, qdot_result* __restrict__ out) {
+  __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
+  __shared__ long long s_qitem[256];
+  __shared__ int s_nqueue;
+  for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
+  if (threadIdx.x == 0) s_nqueue = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    OpPart p;
-    p.sum = 0;
-    for (int k = 0; k < 4; ++k) p.cnt[k] = 0;
-    p.repairs = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      p.sum += s_sum[i];
-      for (int k = 0; k < 4; ++k) p.cnt[k] += s_cnt[i][k];
-      p.repairs += s_cnt[i][4];
+  const int lsb = hdr->lsb;
+  const bool ok = hdr->status == QDOT_OK;
+  const unsigned anchor = (unsigned)(sel->e_max + 2046);  // the bound an exact item recorded
+  const bool f_exact = sel->f == f_spec;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  i128 acc = 0;
+  unsigned long long acc_lo = 0;
+  long long acc_hi = 0;
+  unsigned long long c[5] = {0, 0, 0, 0, 0};
+  const long long G = gridDim.x;
+  for (long long q0 = 0; ok && q0 * G + blockIdx.x < nitems; q0 += blockDim.x) {
+    const long long i = (q0 + threadIdx.x) * G + blockIdx.x;
+    if (i < nitems) {
+      const unsigned long long m = imeta[i];
+      const long long v = isum[i];
+      if (f_exact && !(m & kItemRecompute) && (unsigned)((m >> 12) & 0xFFFu) == anchor) {
+        const unsigned nh = (unsigned)(m >> 24) & 0x1FFu, ns = (unsigned)(m >> 33) & 0x1FFu,
+                       nd = (unsigned)(m >> 42) & 0x1FFu;
+        c[kHalf] += nh;
+        c[kSingle] += ns;
+        c[kDouble] += nd;
+        c[kPerf] += kItem - nh - ns - nd;
+        const int sh = (int)(m & 0xFFFu) - 2046 - 52 - lsb;  // <= L - 52
+        const int sl = min(max(sh, 0), 63), sr = min(max(-sh, 0), 63);
+        const long long wv = v >> sr;
+        const unsigned long long lo = (unsigned long long)wv << sl;
+        acc_lo += lo;
+        acc_hi += ((wv >> 1) >> (63 - sl)) + (acc_lo < lo ? 1 : 0);
+      } else {
+        ++c[4];
+        s_qitem[atomicAdd(&s_nqueue, 1)] = i;  // at most one per thread and round
+      }
     }
-    parts[blockIdx.x] = p;
-    __threadfence();  // the partial is visible before the arrival is counted
-    s_last = atomicAdd(&hdr->done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  // last CTA: the exact sum of the partials, in CTA order, then one rounding
-  __threadfence();
-  const int np = gridDim.x;
-  acc = 0;
-  for (int k = 0; k < 5; ++k) c[k] = 0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    const unsigned long long* pw = reinterpret_cast<const unsigned long long*>(parts + i);
-    const unsigned long long lo = __ldcg(pw), hi = __ldcg(pw + 1);
-    acc += (i128)(((unsigned __int128)hi << 64) | lo);
-    for (int k = 0; k < 4; ++k) c[k] += __ldcg(&parts[i].cnt[k]);
-    c[4] += __ldcg(&parts[i].repairs);
-  }
-  acc = warp_sum_i128(acc);
-  for (int k = 0; k < 5; ++k) c[k] = warp_sum_u64(c[k]);
-  __syncthreads();  // s_sum, s_cnt are reused
-  if (lane == 0) {
-    s_sum[w] = acc;
-    for (int k = 0; k < 5; ++k) s_cnt[w][k] = c[k];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-      acc += s_sum[i];
-      for (int k = 0; k < 5; ++k) c[k] += s_cnt[i][k];
+    __syncthreads();
+    const int nq = s_nqueue;
+    for (int qi = w; qi < nq; qi += (int)(blockDim.x >> 5)) {
+      int u;
+      const long long v = recompute_item(x, y, n, s_qitem[qi], s_lut, lane, &u, c);
+      if (lane == 0 && u != kNone) acc += candidate_to_fixed(v, kSingle, u, 8, lsb);  // grid 2^(u - 52)
     }
-    sel->reserved[0] = (int32_t)(c[4] < 0x7FFFFFFFull ? c[4] : 0x7FFFFFFFull);
-    qdot_result r;
-    r.status = hdr->status;
-    r.n_bins = sel->n_bins;
-    r.e_max = sel->e_max;
-    r.e_min = sel->e_min;
-    r.f = sel->f;
-    for (int k = 0; k < 4; ++k) r.count[k] = (int64_t)c[k];
-    r.count[4] = hdr->zeros;
-    if (r.status != QDOT_OK) {
-      r.value = __longlong_as_double(0x7FF8000000000000ll);
-      r.bound = r.value;
-    } else {
-      r.value = fixed_to_double(acc, hdr->lsb);
-      r.bound = r.n_bins > 0 ? fixed_to_double((i128)r.n_bins, r.e_max + r.f) : 0.0;
-    }
-    *out = r;
+    __syncthreads();
+    if (threadIdx.x == 0) s_nqueue = 0;
+    __syncthreads();
   }
+  acc += (i128)(((unsigned __int128)(unsigned long long)acc_hi << 64) | acc_lo);
+  finish_gather(acc, c, parts, hdr, sel, out);
 }
 
 // The largest k with N * 2^k <= eps (host side; only steers which candidates
@@ -529,10 +838,42 @@ cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_pa
   return cudaGetLastError();
 }
 
+cudaError_t launch_c(const double* x, const double* y, int64_t n, const qdot_params* p, const OnePassPlan& pl,
+                     char* ws, qdot_result* out, cudaStream_t st) {
+  auto* sel = reinterpret_cast<qdot_selection*>(ws + pl.off_sel);
+  auto* hdr = reinterpret_cast<OpHeader*>(ws + pl.off_hdr);
+  auto* wst = reinterpret_cast<WarpStats*>(ws + pl.off_rec);
+  auto* isum = reinterpret_cast<long long*>(ws + pl.off_misc);
+  auto* imeta = reinterpret_cast<unsigned long long*>(ws + pl.off_meta);
+  auto* parts = reinterpret_cast<OpPart*>(ws + pl.off_sel + align_up(sizeof(qdot_selection), 256) +
+                                          align_up(sizeof(OpHeader), 256));
+  const long long nitems = (n + kItem - 1) / kItem;
+  // f if every component is nonzero (a lower bound of the real f)
+  const int f_spec = host_floor_log2_ratio(p->eps, p->split_budget ? (unsigned long long)n : 1ull);
+  const int mh = p->mant_reading ? 11 : 10, ms = p->mant_reading ? 24 : 23;
+  cudaError_t e = cudaMemsetAsync(&hdr->erun, 0x80, sizeof(int), st);  // very negative
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev0, ev1;
+  kernel_events(&ev0, &ev1);
+  if (ev0) cudaEventRecord(ev0, st);
+  static bool smem_set = false;
+  if (!smem_set) {
+    e = cudaFuncSetAttribute(k_onepass_c, cudaFuncAttributeMaxDynamicSharedMemorySize, kOpSmem);
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
+  k_onepass_c<<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, isum, imeta);
+  if (ev1) cudaEventRecord(ev1, st);
+  k_op_select<<<1, 1024, 0, st>>>(wst, pl.grid * kOpWarps, n, *p, sel, hdr);
+  const int gather_grid = 2 * (device_info().sms > 0 ? device_info().sms : 152);  // 2 CTAs per SM
+  k_op_gather_c<<<gather_grid, 256, 0, st>>>(isum, imeta, nitems, f_spec, sel, hdr, parts, x, y, n, out);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool one_pass_supported(int64_t n, const qdot_params* p, bool aligned16) {
-  return aligned16 && n > 0 && p->block >= 32 && p->block <= 256;
+  return aligned16 && n > 0 && (p->block == 1 || (p->block >= 32 && p->block <= 256));
 }
 
 int one_pass_launches(int64_t, const qdot_params*) { return 3; }  // stream, select, gather
@@ -553,6 +894,15 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
   off = align_up(off + sizeof(OpPart) * 4 * sms, 256);  // gather partials
   pl.off_rec = off;
   off = align_up(off + sizeof(WarpStats) * pl.grid * kOpWarps, 256);
+  if (p->block == 1) {  // one record per item: its sum and its meta word
+    const long long nitems = (n + kItem - 1) / kItem;
+    pl.off_misc = off;
+    off = align_up(off + sizeof(long long) * (size_t)nitems, 256);
+    pl.off_meta = off;
+    off = align_up(off + sizeof(unsigned long long) * (size_t)nitems, 256);
+    pl.total = off;
+    return pl;
+  }
   pl.off_misc = off;  // the first candidate slot of every block
   off = align_up(off + sizeof(long long) * (size_t)nblocks, 256);
   pl.off_slot1 = off;  // the second, written for blocks that keep two or more
@@ -572,6 +922,7 @@ cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const q
   char* w = static_cast<char*>(ws);
   cudaError_t e;
   switch (plan.log2b) {
+    case 0: e = launch_c(x, y, n, p, plan, w, out, stream); break;
     case 5: e = launch_lb<5>(x, y, n, p, plan, w, out, stream); break;
     case 6: e = launch_lb<6>(x, y, n, p, plan, w, out, stream); break;
     case 7: e = launch_lb<7>(x, y, n, p, plan, w, out, stream); break;

@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(const double* __restrict__ x
                                                     const int16_t* __restrict__ bkeys, ApplyRec* __restrict__ recs,
                                                     uint8_t* __restrict__ cls_out, double* __restrict__ qx_out,
                                                     double* __restrict__ qy_out) {
-  __shared__ uint8_t s_lut[kKeyCount];
+  __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
   __shared__ i128 s_sum[kWarps];
   __shared__ unsigned long long s_cnt[kWarps][4];
   for (int i = threadIdx.x; i < kKeyCount / 4; i += kThreads)
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_apply_fast(const double* __rest
                                                          const Header* __restrict__ hdr,
                                                          const int16_t* __restrict__ bkeys,
                                                          ApplyRec* __restrict__ recs) {
-  __shared__ uint8_t s_lut[kKeyCount];
+  __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
   __shared__ ClassRound s_tab[5];
   __shared__ i128 s_sum[kWarps];
   __shared__ unsigned long long s_cnt[kWarps][4];

@@ -74,9 +74,9 @@ def test_closed_forms_gpu(q, orc, case):
 @pytest.mark.parametrize("block", [0, 1, 2, 4, 16, 32, 64, 128, 256, 1024])
 @pytest.mark.parametrize("kind", ["a", "b", "c", "cfg0"])
 def test_parity_grid(q, orc, kind, block):
-    # auto takes the fused launch for blocks of 32..256 at these sizes; the
-    # one-pass path is checked explicitly as well
-    paths = ("auto", "one_pass") if 32 <= block <= 256 else ("auto",)
+    # auto takes the fused launch for blocks of 32..256 (and the two-pass one
+    # for blocks of 1) at these sizes; the one-pass path is checked explicitly
+    paths = ("auto", "one_pass") if (32 <= block <= 256 or block == 1) else ("auto",)
     for n in (1, 63, 64, 65, 1000, 4097, 100003):
         x, y = workloads.pair(kind, n, 17 + n)
         for eps in (1e-16, 1e-8, 1e-3, 0.5):
@@ -92,6 +92,8 @@ def test_split_and_mant_readings(q, orc, block):
         for mant in (0, 1):
             for eps in (1e-12, 1e-6, 1e-2):
                 _check(q, orc, x, y, eps, block, split=split, mant=mant)
+                if block > 0:
+                    _check(q, orc, x, y, eps, block, split=split, mant=mant, explain=False, path="one_pass")
 
 
 @pytest.mark.parametrize("block", [0, 1, 8, 32, 64, 512])
@@ -139,6 +141,8 @@ def test_edge_cases(q, orc):
     for block in (0, 1, 2, 8):
         for eps in (1e-16, 1e-3, 10.0):
             _check(q, orc, x, y, eps, block)
+            if block == 1:
+                _check(q, orc, x, y, eps, block, explain=False, path="one_pass")
 
 
 def test_invalid_arguments_raise(q):
@@ -225,6 +229,36 @@ def test_one_pass_recompute_path(q, orc, block):
     assert r.count == tuple(ref.count)
     assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
     assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
+
+
+@pytest.mark.parametrize("eps", [1e-15, 1e-8, 1e-3, 10.0])
+def test_one_pass_components(q, orc, eps):
+    """Blocks of one component in one pass.  An item of 256 components is
+    accepted when the warp's bound of e_max was exact and f equals f_spec, and
+    recomputed otherwise: a ramp (the bound lags), a ramp whose last component
+    dwarfs the rest, and vectors where a third of the products are zero (so
+    f > f_spec and every item is recomputed).  Results must match the oracle."""
+    import ctypes
+    lib = q.load()
+    n = (1 << 21) + 77
+    rng = np.random.default_rng(29)
+    ramp = np.exp2(np.linspace(0.0, 60.0, n)) * rng.uniform(1.0, 2.0, n)
+    spike = ramp.copy()
+    spike[-1] = 2.0**80
+    sparse, ys = workloads.pair("b", n, 41)
+    sparse[rng.random(n) < 0.34] = 0.0
+    y = rng.uniform(-2.0, 2.0, n)
+    for x, yy, need_rep in ((ramp, y, False), (spike, y, True), (sparse, ys, True)):
+        r, rep = _repairs(q, x, yy, eps, 1)
+        ref = orc.qdot(x, yy, eps=eps, block=1)
+        assert r.count == tuple(ref.count)
+        assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
+        assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, yy)
+        if need_rep:
+            assert rep > 0
+    p = q.params(1e-8, 1, 1, 0, "auto")
+    assert lib.qdot_select_path(1 << 24, ctypes.byref(p), 1) == 2  # QDOT_PATH_ONE_PASS
+    assert lib.qdot_select_path((1 << 24) - 1, ctypes.byref(p), 1) == 1  # QDOT_PATH_TWO_PASS
 
 
 @pytest.mark.parametrize("block", [32, 64, 128, 256])
