@@ -848,7 +848,7 @@ def main():
         cg = cg_summary(args)
 
     peak, peak_src = measured_peak_hbm()
-    kernel = {2: "k_onepass", 4: "k_qdot_fused"}.get(lib.qdot_select_path(n, ctypes.byref(p), 1), "k_apply_fast")
+    kernel = lib.qdot_stream_kernel(n, ctypes.byref(p), 1).decode()
     achieved = 16.0 * n / (kern_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

@@ -328,6 +328,13 @@ int32_t qdot_kernel_launches(int64_t n, const qdot_params* p, int32_t aligned16)
  * QDOT_PATH_ONE_PASS or QDOT_PATH_TWO_PASS (0 on invalid parameters). */
 int32_t qdot_select_path(int64_t n, const qdot_params* p, int32_t aligned16);
 
+/* Name of the streaming kernel qdot() runs for these arguments (the one the
+ * measurement hook below times): "k_qdot_fused", "k_onepass" (block
+ * records), "k_onepass_items" (item records: blocks of one component) or
+ * "k_apply_fast" (two-pass); "" on invalid parameters.
+ * A static string. */
+const char* qdot_stream_kernel(int64_t n, const qdot_params* p, int32_t aligned16);
+
 /* Measurement hook.  When begin and end are both non-NULL (cudaEvent_t
  * handles created by the caller), every later qdot() on the calling thread
  * records `begin` on the call's stream right before its main streaming kernel

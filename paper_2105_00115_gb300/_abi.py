@@ -86,6 +86,7 @@ SIGNATURES = {
     "qdot_static_scratch": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP]),
     "qdot_kernel_launches": (_I32, [_I64, _PP, _I32]),
     "qdot_select_path": (_I32, [_I64, _PP, _I32]),
+    "qdot_stream_kernel": (ctypes.c_char_p, [_I64, _PP, _I32]),
     "qdot_set_kernel_events": (None, [_VP, _VP]),
     "qdot_last_error": (ctypes.c_char_p, []),
     "qdot_version": (ctypes.c_char_p, []),

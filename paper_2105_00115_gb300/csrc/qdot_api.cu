@@ -354,6 +354,15 @@ int32_t qdot_select_path(int64_t n, const qdot_params* p, int32_t al16) {
   return c == kFused ? QDOT_PATH_FUSED : (c == kOnePass ? QDOT_PATH_ONE_PASS : QDOT_PATH_TWO_PASS);
 }
 
+const char* qdot_stream_kernel(int64_t n, const qdot_params* p, int32_t al16) {
+  std::string why;
+  if (!valid_params(n, p, &why)) return "";
+  const PathChoice c = choose_path(n, p, al16 != 0);
+  if (c == kFused) return "k_qdot_fused";
+  if (c == kOnePass) return one_pass_stream_kernel(n, p);
+  return "k_apply_fast";
+}
+
 void qdot_set_kernel_events(void* begin, void* end) {
   g_ev_begin = (begin && end) ? static_cast<cudaEvent_t>(begin) : nullptr;
   g_ev_end = (begin && end) ? static_cast<cudaEvent_t>(end) : nullptr;

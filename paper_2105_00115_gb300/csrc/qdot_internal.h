@@ -59,12 +59,14 @@ struct OnePassPlan {
   int window = 0;         // keys kept per record
   long long units = 0;    // work units (each produces one record)
   long long unit_blocks = 0;
+  bool items = false;  // item records (one per 256 components) instead of block records
   size_t off_sel = 0, off_hdr = 0, off_rec = 0, off_misc = 0, off_slot1 = 0, off_meta = 0, off_slot3 = 0;
   size_t rec_bytes = 0;
   size_t total = 0;
 };
 bool one_pass_supported(int64_t n, const qdot_params* p, bool aligned16);
 OnePassPlan plan_one_pass(int64_t n, const qdot_params* p);
+const char* one_pass_stream_kernel(int64_t n, const qdot_params* p);
 int one_pass_launches(int64_t n, const qdot_params* p);
 cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const qdot_params* p,
                             const OnePassPlan& plan, void* ws, qdot_result* out, qdot_selection* sel,

@@ -91,6 +91,19 @@ constexpr int kCalm = 4;
 // read kExchange items later (the first read, at item 1, at item 2).
 constexpr int kExchange = 2;
 
+// Blocks of 32: from this n on, one-pass qdot keeps one record per item of
+// 256 components (classes per block, the item summed on its own grid and
+// recomputed if the bound of e_max it used was not exact) instead of
+// candidate records per block.  Below it, warps have too few items for the
+// bound to settle early.  Larger blocks keep the block records: with 4 or
+// fewer blocks per item their gather is already short, and the items every
+// warp recomputes (its first two) would cost more than they save.
+constexpr long long kItemPathMinN = 1ll << 25;
+// Off: the item records for blocks of 32 are built and measured faster, but
+// a fix to them (every lane now joins the block shuffles of the statistics
+// branch) has not yet run on a GPU.
+constexpr bool kItemPathForBlocks = false;
+
 // Blocks a gather CTA can queue for recomputation by its warps together.
 constexpr int kRepairQueue = 512;
 
@@ -571,17 +584,22 @@ __device__ __forceinline__ void acc_components_mode(unsigned rmode, const Chunk&
   }
 }
 
-// Streaming kernel for B = 1: every component is quantized to the class of
-// its score key - e_lo - f_spec + 1, which is its true score if the warp's
-// bound e_lo equals e_max and f equals f_spec (N_bins = n, no zeros).
-__global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_c(const double* __restrict__ x,
-                                                             const double* __restrict__ y, long long n, int f_spec,
-                                                             int mh, int ms, int* __restrict__ erun,
-                                                             WarpStats* __restrict__ wstats,
-                                                             long long* __restrict__ isum,
-                                                             unsigned long long* __restrict__ imeta) {
-  constexpr int LOG2B = 8;  // the item layout of blocks of 256
+// Streaming kernel with item records.  LOG2B = 0: blocks of one component,
+// each quantized to the class of its score key - e_lo - f_spec + 1.  LOG2B =
+// 5..8: blocks of 2^LOG2B, each block's components to the class of the block
+// score log2 B + u_b - e_lo - f_spec + 1.  Either is the true score if the
+// warp's bound e_lo equals e_max and f equals f_spec (no empty blocks).
+template <int LOG2B>
+__global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(const double* __restrict__ x,
+                                                                 const double* __restrict__ y, long long n,
+                                                                 int f_spec, int mh, int ms, int* __restrict__ erun,
+                                                                 WarpStats* __restrict__ wstats,
+                                                                 long long* __restrict__ isum,
+                                                                 unsigned long long* __restrict__ imeta) {
+  constexpr int LB = LOG2B ? LOG2B : 8;  // the item layout (blocks of one: that of 256)
+  constexpr int L = Map<LB>::L;
   const int lane = threadIdx.x & 31;
+  const int sub = lane % L;
   long long nbins = 0, zeros_l = 0;
   int emax_l = kNone, kmin = INT_MAX, bad = 0;
   const long long nitems = (n + kItem - 1) / kItem;
@@ -593,7 +611,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_c(const do
 #pragma unroll
   for (int st = 0; st < kStages - 1; ++st) {
     const long long item = gwarp + st * nwarps;
-    if (item < nitems) issue_item<LOG2B>(x, y, n, item, lane, ring + st * kStageWords);
+    if (item < nitems) issue_item<LB>(x, y, n, item, lane, ring + st * kStageWords);
     cp_async_commit();
   }
   int stage = 0;
@@ -603,11 +621,11 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_c(const do
     {
       const long long ahead = it + (long long)(kStages - 1) * nwarps;
       const int st = stage == 0 ? kStages - 1 : stage - 1;
-      if (ahead < nitems) issue_item<LOG2B>(x, y, n, ahead, lane, ring + st * kStageWords);
+      if (ahead < nitems) issue_item<LB>(x, y, n, ahead, lane, ring + st * kStageWords);
       cp_async_commit();
     }
     cp_async_wait<kStages - 1>();
-    read_item<LOG2B>(ring + stage * kStageWords, n, it, lane, cur);
+    read_item<LB>(ring + stage * kStageWords, n, it, lane, cur);
     stage = stage == kStages - 1 ? 0 : stage + 1;
     int key[8];
     int cmax = kNone;
@@ -617,19 +635,30 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_c(const do
       const int u = __reduce_max_sync(0xffffffffu, cmax);  // the item's largest key (biased)
       track_bound(u, lane, iter, erun, e_lo, pending, raised);
       const int a = e_lo + f_spec - 1;  // score = key - a
-      int cls[8];
-      unsigned seen = 0, cnt = 0;  // classes present; per-class counts in 8-bit fields
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int sg = key[j] - a;
-        cls[j] = sg < 0 ? kPerf : (sg < mh ? kHalf : (sg < ms ? kSingle : kDouble));
-        seen |= 1u << cls[j];
-        cnt += 1u << (cls[j] << 3);
-      }
-      seen = __reduce_or_sync(0xffffffffu, seen);
-      const unsigned rmode = ((seen >> kSingle) & 1u) | (((seen >> kHalf) & 1u) << 1) | ((seen & 1u) << 2);
       double aF = 0.0;
-      acc_components_mode(rmode, cur, key, u, cls, aF);
+      unsigned cnt = 0;  // per-class counts of the lane's components, 8-bit fields
+      if (LOG2B == 0) {
+        int cls[8];
+        unsigned seen = 0;  // classes present
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int sg = key[j] - a;
+          cls[j] = sg < 0 ? kPerf : (sg < mh ? kHalf : (sg < ms ? kSingle : kDouble));
+          seen |= 1u << cls[j];
+          cnt += 1u << (cls[j] << 3);
+        }
+        seen = __reduce_or_sync(0xffffffffu, seen);
+        const unsigned rmode = ((seen >> kSingle) & 1u) | (((seen >> kHalf) & 1u) << 1) | ((seen & 1u) << 2);
+        acc_components_mode(rmode, cur, key, u, cls, aF);
+      } else {
+        const int sg = LB + group_max<L>(cmax) - a;  // the block's score (M_b = B)
+        const int cls = sg < 0 ? kPerf : (sg < mh ? kHalf : (sg < ms ? kSingle : kDouble));
+        const unsigned prim = cls == kPerf ? 0u : 1u << cls;
+        long long aH = 0, aS = 0;
+        acc_lane_mask<LB>(__reduce_or_sync(0xffffffffu, prim), 0u, cur, key, u, prim, aH, aS, aF);
+        if (!prim) aF = 0.0;  // a perforated block adds nothing
+        cnt = 8u << (cls << 3);
+      }
       long long v = __double2ll_rz(aF * 4503599627370496.0);  // onto the grid 2^(u - 52)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -638,10 +667,10 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_c(const do
       slot = v;
       meta = (unsigned long long)u | ((unsigned long long)e_lo << 12) | ((unsigned long long)(hd & 0xFFFFu) << 24) |
              ((unsigned long long)(ps >> 16) << 33) | ((unsigned long long)(hd >> 16) << 42);
-      nbins += 8;
+      nbins += LOG2B == 0 ? 8 : (sub == 0);  // nonzero components, or non-empty blocks
       emax_l = max(emax_l, u - 2046);
     } else {  // statistics only; the gather recomputes the item
-      int wmax = kNone;
+      int wmax = kNone, nz = 0;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const uint64_t a = cur.x[j], b = cur.y[j];
@@ -652,10 +681,16 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_c(const do
         zeros_l += in && fin && z;
         if (in && fin && !z) {
           const int k = exponent_of(a) + exponent_of(b) + 2046;
-          ++nbins;
+          ++nz;
           kmin = min(kmin, k);
           wmax = max(wmax, k);
         }
+      }
+      if (LOG2B == 0) {
+        nbins += nz;
+      } else {  // non-empty blocks; every lane takes part in the block's shuffles
+        const int block_nz = group_sum_i<L>(nz);
+        nbins += (sub == 0 && block_nz > 0);
       }
       wmax = __reduce_max_sync(0xffffffffu, wmax);
       track_bound(wmax, lane, iter, erun, e_lo, pending, raised);
@@ -687,9 +722,11 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_c(const do
 }
 
 // One item recomputed by a warp with the final classes: lane l takes the
-// components item*256 + l + 32k (coalesced).  Returns the item's sum on the
-// grid 2^(u - 52) (u its largest key, unbiased, in *u_out; kNone if the item
-// has no nonzero component) and adds the lane's class counts to c.
+// components item*256 + l + 32k (coalesced), so slice k lies in block
+// (l + 32k) >> LOG2B of the item.  Returns the item's sum on the grid
+// 2^(u - 52) (u its largest key, unbiased, in *u_out; kNone if the item has
+// no nonzero component) and adds the lane's class counts to c.
+template <int LOG2B>
 __device__ long long recompute_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
                                     long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
                                     unsigned long long (&c)[5]) {
@@ -708,14 +745,34 @@ __device__ long long recompute_item(const double* __restrict__ x, const double* 
   u = __reduce_max_sync(0xffffffffu, u);
   *u_out = u;
   if (u == kNone) return 0;
+  int cls[8];
+  if (LOG2B == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cls[k] = e[k] == kNone ? kPerf : lut[e[k] - kKeyMin];
+  } else {
+    constexpr int KPB = (1 << LOG2B) / 32;  // slices per block
+#pragma unroll
+    for (int b = 0; b < 8 / KPB; ++b) {
+      int ub = kNone, mb = 0;
+#pragma unroll
+      for (int kk = 0; kk < KPB; ++kk) {
+        const int k = b * KPB + kk;
+        ub = max(ub, __reduce_max_sync(0xffffffffu, e[k]));
+        mb += __popc(__ballot_sync(0xffffffffu, e[k] != kNone));
+      }
+      const int cb = mb ? lut[ceil_log2_u32((uint32_t)mb) + ub - kKeyMin] : kPerf;  // the block key s_b
+#pragma unroll
+      for (int kk = 0; kk < KPB; ++kk) cls[b * KPB + kk] = cb;
+    }
+  }
   long long aH = 0, aS = 0;
   double aD = 0.0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     if (e[k] == kNone) continue;
-    const int cls = lut[e[k] - kKeyMin];
-    c[cls] += 1;
-    if (cls != kPerf) component_candidates<8>(xa[k], ya[k], e[k] + 2046, u + 2046, 1u << cls, aH, aS, aD);
+    c[cls[k]] += 1;
+    if (cls[k] != kPerf)
+      component_candidates<8>(xa[k], ya[k], e[k] + 2046, u + 2046, 1u << cls[k], aH, aS, aD);
   }
   long long v = aH + aS + __double2ll_rz(aD * 4503599627370496.0);
 #pragma unroll
@@ -723,13 +780,60 @@ __device__ long long recompute_item(const double* __restrict__ x, const double* 
   return v;
 }
 
-// Gather for B = 1: an item whose bound e_lo was e_max, and f_spec f, adds
+// recompute_item() on the streaming kernel's arithmetic, for an item whose
+// components are all in range, nonzero, normal and finite: the lanes load it
+// in the streaming layout and quantize with the final classes from the table
+// (per component, or per block from the block key log2 B + u_b).  Any other
+// item goes to recompute_item().
+template <int LOG2B>
+__device__ long long recompute_item_fast(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                         long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
+                                         unsigned long long (&c)[5]) {
+  constexpr int LB = LOG2B ? LOG2B : 8;
+  constexpr int L = Map<LB>::L;
+  Chunk ch;
+  load_item<LB>(x, y, n, item, lane, ch);
+  int key[8];
+  int cmax = kNone, kmin = INT_MAX;
+  if (!__all_sync(0xffffffffu, chunk_keys(ch, key, cmax, kmin)))
+    return recompute_item<LOG2B>(x, y, n, item, lut, lane, u_out, c);
+  const int u = __reduce_max_sync(0xffffffffu, cmax);  // biased
+  *u_out = u - 2046;
+  double aF = 0.0;
+  if (LOG2B == 0) {
+    int cls[8];
+    unsigned seen = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      cls[j] = lut[key[j] - 2046 - kKeyMin];
+      seen |= 1u << cls[j];
+      c[cls[j]] += 1;
+    }
+    seen = __reduce_or_sync(0xffffffffu, seen);
+    acc_components_mode(((seen >> kSingle) & 1u) | (((seen >> kHalf) & 1u) << 1) | ((seen & 1u) << 2), ch, key, u,
+                        cls, aF);
+  } else {
+    const int cls = lut[LB + group_max<L>(cmax) - 2046 - kKeyMin];  // the block key s_b = log2 B + u_b
+    c[cls] += 8;
+    const unsigned prim = cls == kPerf ? 0u : 1u << cls;
+    long long aH = 0, aS = 0;
+    acc_lane_mask<LB>(__reduce_or_sync(0xffffffffu, prim), 0u, ch, key, u, prim, aH, aS, aF);
+    if (!prim) aF = 0.0;
+  }
+  long long v = __double2ll_rz(aF * 4503599627370496.0);  // grid 2^(u - 52)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Gather of item records: an item whose bound e_lo was e_max, and f_spec f, adds
 // its record; any other item is recomputed with the final classes.  The CTA
 // takes 256 items at a time, one per thread, and its warps recompute the
 // rejected ones of each round together.  Items are dealt to the CTAs in turn
 // (item i to CTA i mod grid): the rejected items are mostly every warp's
 // first few, at the start of the vectors, and this spreads them evenly.
-__global__ void __launch_bounds__(256, 2) k_op_gather_c(const long long* __restrict__ isum,
+template <int LOG2B>
+__global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __restrict__ isum,
                                                      const unsigned long long* __restrict__ imeta, long long nitems,
                                                      int f_spec, qdot_selection* __restrict__ sel,
                                                      OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
@@ -779,7 +883,7 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_c(const long long* __restr
     const int nq = s_nqueue;
     for (int qi = w; qi < nq; qi += (int)(blockDim.x >> 5)) {
       int u;
-      const long long v = recompute_item(x, y, n, s_qitem[qi], s_lut, lane, &u, c);
+      const long long v = recompute_item_fast<LOG2B>(x, y, n, s_qitem[qi], s_lut, lane, &u, c);
       if (lane == 0 && u != kNone) acc += candidate_to_fixed(v, kSingle, u, 8, lsb);  // grid 2^(u - 52)
     }
     __syncthreads();
@@ -838,8 +942,9 @@ cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_pa
   return cudaGetLastError();
 }
 
-cudaError_t launch_c(const double* x, const double* y, int64_t n, const qdot_params* p, const OnePassPlan& pl,
-                     char* ws, qdot_result* out, cudaStream_t st) {
+template <int LOG2B>
+cudaError_t launch_items(const double* x, const double* y, int64_t n, const qdot_params* p, const OnePassPlan& pl,
+                         char* ws, qdot_result* out, cudaStream_t st) {
   auto* sel = reinterpret_cast<qdot_selection*>(ws + pl.off_sel);
   auto* hdr = reinterpret_cast<OpHeader*>(ws + pl.off_hdr);
   auto* wst = reinterpret_cast<WarpStats*>(ws + pl.off_rec);
@@ -848,8 +953,9 @@ cudaError_t launch_c(const double* x, const double* y, int64_t n, const qdot_par
   auto* parts = reinterpret_cast<OpPart*>(ws + pl.off_sel + align_up(sizeof(qdot_selection), 256) +
                                           align_up(sizeof(OpHeader), 256));
   const long long nitems = (n + kItem - 1) / kItem;
-  // f if every component is nonzero (a lower bound of the real f)
-  const int f_spec = host_floor_log2_ratio(p->eps, p->split_budget ? (unsigned long long)n : 1ull);
+  // f if every block is non-empty (a lower bound of the real f)
+  const long long nblocks = LOG2B ? (n + (1ll << LOG2B) - 1) >> LOG2B : n;
+  const int f_spec = host_floor_log2_ratio(p->eps, p->split_budget ? (unsigned long long)nblocks : 1ull);
   const int mh = p->mant_reading ? 11 : 10, ms = p->mant_reading ? 24 : 23;
   cudaError_t e = cudaMemsetAsync(&hdr->erun, 0x80, sizeof(int), st);  // very negative
   if (e != cudaSuccess) return e;
@@ -858,15 +964,17 @@ cudaError_t launch_c(const double* x, const double* y, int64_t n, const qdot_par
   if (ev0) cudaEventRecord(ev0, st);
   static bool smem_set = false;
   if (!smem_set) {
-    e = cudaFuncSetAttribute(k_onepass_c, cudaFuncAttributeMaxDynamicSharedMemorySize, kOpSmem);
+    e = cudaFuncSetAttribute(k_onepass_items<LOG2B>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOpSmem);
     if (e != cudaSuccess) return e;
     smem_set = true;
   }
-  k_onepass_c<<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, isum, imeta);
+  k_onepass_items<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, isum,
+                                                                 imeta);
   if (ev1) cudaEventRecord(ev1, st);
   k_op_select<<<1, 1024, 0, st>>>(wst, pl.grid * kOpWarps, n, *p, sel, hdr);
   const int gather_grid = 2 * (device_info().sms > 0 ? device_info().sms : 152);  // 2 CTAs per SM
-  k_op_gather_c<<<gather_grid, 256, 0, st>>>(isum, imeta, nitems, f_spec, sel, hdr, parts, x, y, n, out);
+  k_op_gather_items<LOG2B><<<gather_grid, 256, 0, st>>>(isum, imeta, nitems, f_spec, sel, hdr, parts, x, y, n,
+                                                         out);
   return cudaGetLastError();
 }
 
@@ -877,6 +985,10 @@ bool one_pass_supported(int64_t n, const qdot_params* p, bool aligned16) {
 }
 
 int one_pass_launches(int64_t, const qdot_params*) { return 3; }  // stream, select, gather
+
+const char* one_pass_stream_kernel(int64_t n, const qdot_params* p) {
+  return plan_one_pass(n, p).items ? "k_onepass_items" : "k_onepass";
+}
 
 OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
   OnePassPlan pl;
@@ -894,7 +1006,8 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
   off = align_up(off + sizeof(OpPart) * 4 * sms, 256);  // gather partials
   pl.off_rec = off;
   off = align_up(off + sizeof(WarpStats) * pl.grid * kOpWarps, 256);
-  if (p->block == 1) {  // one record per item: its sum and its meta word
+  pl.items = p->block == 1 || (kItemPathForBlocks && p->block == 32 && n >= kItemPathMinN);
+  if (pl.items) {  // one record per item: its sum and its meta word
     const long long nitems = (n + kItem - 1) / kItem;
     pl.off_misc = off;
     off = align_up(off + sizeof(long long) * (size_t)nitems, 256);
@@ -922,11 +1035,11 @@ cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const q
   char* w = static_cast<char*>(ws);
   cudaError_t e;
   switch (plan.log2b) {
-    case 0: e = launch_c(x, y, n, p, plan, w, out, stream); break;
-    case 5: e = launch_lb<5>(x, y, n, p, plan, w, out, stream); break;
-    case 6: e = launch_lb<6>(x, y, n, p, plan, w, out, stream); break;
-    case 7: e = launch_lb<7>(x, y, n, p, plan, w, out, stream); break;
-    default: e = launch_lb<8>(x, y, n, p, plan, w, out, stream); break;
+    case 0: e = launch_items<0>(x, y, n, p, plan, w, out, stream); break;
+    case 5: e = plan.items ? launch_items<5>(x, y, n, p, plan, w, out, stream) : launch_lb<5>(x, y, n, p, plan, w, out, stream); break;
+    case 6: e = plan.items ? launch_items<6>(x, y, n, p, plan, w, out, stream) : launch_lb<6>(x, y, n, p, plan, w, out, stream); break;
+    case 7: e = plan.items ? launch_items<7>(x, y, n, p, plan, w, out, stream) : launch_lb<7>(x, y, n, p, plan, w, out, stream); break;
+    default: e = plan.items ? launch_items<8>(x, y, n, p, plan, w, out, stream) : launch_lb<8>(x, y, n, p, plan, w, out, stream); break;
   }
   if (e != cudaSuccess) return e;
   if (sel) e = cudaMemcpyAsync(sel, w + plan.off_sel, sizeof(qdot_selection), cudaMemcpyDeviceToDevice, stream);

@@ -52,6 +52,22 @@ def test_version(lib):
     assert b"sm_103a" in lib.qdot_version()
 
 
+def test_stream_kernel_names(lib):
+    """The streaming kernel each (n, block, alignment) selects (host logic)."""
+    import paper_2105_00115_gb300 as q
+
+    def name(n, block, al16=1):
+        return lib.qdot_stream_kernel(n, ctypes.byref(q.params(eps=1e-8, block=block)), al16)
+
+    assert name(1 << 28, 32) == b"k_onepass" and name(1 << 25, 32) == b"k_onepass"
+    assert name(1 << 20, 32) in (b"k_onepass", b"k_qdot_fused")
+    assert name(1 << 28, 64) == b"k_onepass" and name(1 << 28, 256) == b"k_onepass"
+    assert name(1 << 28, 1) == b"k_onepass_items" and name(1 << 20, 1) == b"k_apply_fast"
+    assert name(1 << 28, 0) == b"k_apply_fast" and name(1 << 28, 8) == b"k_apply_fast"
+    assert name(1 << 28, 32, al16=0) == b"k_apply_fast"  # 8-byte aligned inputs
+    assert name(1 << 20, 3) == b""  # invalid block
+
+
 def test_workspace_size_rejects_bad_params(lib):
     import paper_2105_00115_gb300 as q
     ok = q.params(eps=1e-8, block=32)
