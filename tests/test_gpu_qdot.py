@@ -261,6 +261,33 @@ def test_one_pass_components(q, orc, eps):
     assert lib.qdot_select_path((1 << 24) - 1, ctypes.byref(p), 1) == 1  # QDOT_PATH_TWO_PASS
 
 
+@pytest.mark.parametrize("eps", [1e-8, 1e-3])
+def test_one_pass_items_blocks_of_32(q, orc, eps):
+    """Blocks of 32 with item records (when the library takes them, from
+    n = 2^25): the classes per block, the item summed on its own grid and
+    recomputed when the bound of e_max it used was not exact (every warp's
+    first items at least).  Uniform+outliers with a ragged end, a ramp (the
+    bound lags) and vectors with zeros (the general recompute) must match
+    the oracle."""
+    import ctypes
+    lib = q.load()
+    n = (1 << 25) + 333
+    if lib.qdot_stream_kernel(n, ctypes.byref(q.params(eps, 32, 1, 0, "auto")), 1) != b"k_onepass_items":
+        pytest.skip("this build keeps blocks of 32 on block records")
+    rng = np.random.default_rng(31)
+    x, y = workloads.pair("c", n, 77)
+    ramp = x * np.exp2(np.linspace(0.0, 40.0, n))
+    sparse = x.copy()
+    sparse[rng.random(n) < 0.01] = 0.0
+    for xx in (x, ramp, sparse):
+        r, rep = _repairs(q, xx, y, eps, 32)
+        ref = orc.qdot(xx, y, eps=eps, block=32)
+        assert rep > 0
+        assert r.count == tuple(ref.count)
+        assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
+        assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(xx, y)
+
+
 @pytest.mark.parametrize("block", [32, 64, 128, 256])
 def test_fused_path(q, orc, block):
     """One cooperative launch (the solvers' sizes): parity with the oracle and
