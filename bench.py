@@ -171,6 +171,69 @@ def recorded_traffic(kernel: str, n: int):
     return float(ent["dram_bytes"]) * n / float(ent["n"])
 
 
+def host_cpu():
+    """(logical cores, CPU model string) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count(), model
+
+
+def best_of(fn, reps):
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return min(ts)
+
+
+def cpu_baselines(x, y, args):
+    """The oracle as it stands, single thread, on a bounded sample of the same
+    x, y (the reported cpu_baseline), plus host context: the same exact
+    computation spread over every host core (threads' exact accumulators added
+    exactly) and a plain FP64 dot on one core and on all of them; best of
+    several runs each."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    n = x.shape[0]
+    cores, model = host_cpu()
+    threads = oracle.max_threads()
+    m1 = min(n, 1 << 25)
+    xs, ys = np.ascontiguousarray(x[:m1]), np.ascontiguousarray(y[:m1])
+    t1 = best_of(lambda: oracle.qdot(xs, ys, eps=args.eps, block=args.block), 2)
+    mt = min(n, 1 << 26)
+    xt, yt = np.ascontiguousarray(x[:mt]), np.ascontiguousarray(y[:mt])
+    tt = best_of(lambda: oracle.qdot_threads(xt, yt, eps=args.eps, block=args.block, threads=threads), 3)
+    td1 = best_of(lambda: oracle.dot_fp64(xt, yt, 1), 3)
+    tdt = best_of(lambda: oracle.dot_fp64(xt, yt, threads), 5)
+    gbs = lambda m, t: 16.0 * m / t / 1e9  # noqa: E731
+    return {"value": gbs(m1, t1), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first 2^{m1.bit_length() - 1} of the 2^{n.bit_length() - 1} components of the same x, y "
+                      f"(best of 2, {t1:.1f} s each, single thread)",
+            "host_cores": cores, "cpu_model": model,
+            "threaded_oracle": {"value": gbs(mt, tt), "unit": "GB/s", "threads": threads,
+                                "sample": f"first 2^{mt.bit_length() - 1} components, best of 3"},
+            "fp64_dot": {"one_core_gbs": gbs(mt, td1), "all_cores_gbs": gbs(mt, tdt), "threads": threads,
+                         "sample": f"first 2^{mt.bit_length() - 1} components, best of 3 / 5"}}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores, each
     step a bounded sample of the same workload."""
@@ -191,11 +254,16 @@ def run_reference(args, rank, world):
     total = sum(times)
     gbs = 16.0 * m * args.steps / total / 1e9
     sample = f"first 2^{m.bit_length() - 1} components of the {DIST_NAMES[args.dist]} workload per step"
+    cores, model = host_cpu()
+    config = workload_config(args)
+    config["n"] = m  # the components each step times
+    config["sample_of_n"] = args.n
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args),
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host_cores": cores, "cpu_model": model},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -463,7 +531,7 @@ def run_cg_batched(args, rank, world, local, dist, lib):
 
 
 def run_paper(args, rank, world, local, dist, lib):
-    """The paper's synthetic experiments (Sec. 6.1) on the GPU:
+    """The paper's synthetic experiments (Sec. 4.1) on the GPU:
     - bound tightness: eps = 1e-16, n in 1e2 .. 1e7, distributions A (t in
       {10, 15, .., 100}) and B (t in {2, 4, .., 30}); qdot_bound - relerr per pair;
     - effectiveness, speedup and efficiency (the paper's eqs. approx-effect,
@@ -562,7 +630,7 @@ def run_paper(args, rank, world, local, dist, lib):
     worst_tight = min(r["min_bound_minus_relerr_vs_fp64_dot"] for r in tight
                       if r["min_bound_minus_relerr_vs_fp64_dot"] is not None)
     return {
-        "metric": "qdot approximation effectiveness, speedup and efficiency (paper Sec. 6.1 synthetic data)",
+        "metric": "qdot approximation effectiveness, speedup and efficiency (paper Sec. 4.1 synthetic data)",
         "value": statistics.median(r["efficiency"] for r in rows), "unit": "efficiency (median)", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -832,16 +900,7 @@ def main():
     # CPU baseline: the oracle on a bounded prefix of the same data (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        m = min(n, 1 << 26)
-        xs, ys = np.ascontiguousarray(x[:m]), np.ascontiguousarray(y[:m])
-        c0 = time.perf_counter()
-        oracle.qdot(xs, ys, eps=args.eps, block=args.block)
-        c_s = time.perf_counter() - c0
-        cpu = {"value": 16.0 * m / c_s / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"first 2^{m.bit_length() - 1} of the 2^{n.bit_length() - 1} components of the same x, y "
-                         f"({c_s:.1f} s, single thread)"}
+        cpu = cpu_baselines(x, y, args)
 
     cg = None
     if not args.no_cg and rank == 0:

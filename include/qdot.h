@@ -21,7 +21,7 @@
  *             they belong to no bin and contribute exactly 0.
  *   bins      block == 0: exact binning, one bin per distinct key (Sec. 3.2);
  *             block == B: the non-ZERO components of each index block
- *             [bB, (b+1)B), u_b = max key, M_b = count (Sec. 5, blocked approach).
+ *             [bB, (b+1)B), u_b = max key, M_b = count (Sec. 5, the blocked approach of the conclusion).
  *   f         floor(log2(eps / N_bins)) (split_budget = 1, Sec. 4.1) or
  *             floor(log2 eps) (split_budget = 0), computed exactly.
  *   sigma_k   ceil(log2 M_k) + u_k - e_max - f + 1 (eq. bin-score-def).
@@ -306,19 +306,74 @@ qdot_status qdot_from_host(const double* x_host, const double* y_host, int64_t n
  *   x, y, n, p, out, stream  as for qdot(); always the two-pass path.
  * Scratch: a fixed array of QDOT_STATIC_SCRATCH_BYTES inside the library,
  * held by every GPU that loads the library until the process exits.  It
- * fits any n for exact binning and blocks of up to 64 components; larger
- * blocks need 2 bytes per block on top of a fixed ~90 KB, so n is limited to
- * about B * 480000.  Arguments that do not fit return QDOT_ERR_WORKSPACE with
- * a message, before anything is launched.  Nothing is allocated: no
- * cudaMalloc, cudaFree or allocating library call.
+ * fits any n for exact binning, blocks of one component, and blocks of up to
+ * 64 components when x and y are 16-byte aligned (up to 32 when they are
+ * only 8-byte aligned); larger blocks need 2 bytes per block on top of a
+ * fixed ~90 KB, so n is limited to about B * 480000.  Arguments that do not
+ * fit return QDOT_ERR_WORKSPACE with a message, before anything is launched.
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array, which keeps the
- * last call's contents; each call clears what it needs cleared, but calls
- * whose executions overlap on the GPU (for example on two streams) race on
- * the array and must be serialised by the caller. */
+ * before any stream capture.  The address is cached per device with the
+ * context it belongs to, and looked up again in a new context (after
+ * cudaDeviceReset()).  All calls share the one array, which keeps the last
+ * call's contents; each call clears what it needs cleared, but calls whose
+ * executions overlap on the GPU (for example on two streams) race on the
+ * array and must be serialised by the caller. */
 qdot_status qdot_static_scratch(const double* x, const double* y, int64_t n, const qdot_params* p,
                                 qdot_result* out, void* stream);
+
+/* Per-unit record of qdot_trace() (16 bytes): what the selection decided for
+ * one unit of work of the streaming kernels and what the final sum took from
+ * it.  A unit is a block of B components (blocked binning with block records)
+ * or a warp item of 256 consecutive components (item records: blocks of one
+ * component, and blocks of 32 where the library keeps item records). */
+typedef struct {
+  int64_t value;     /* the unit's contribution is value * 2^grid, exactly; the
+                        final fixed-point sum truncates it to its own grid
+                        2^(e_max - L) (see z above) */
+  int32_t grid;
+  uint8_t cls;       /* block units: the block's class (QDOT_PERF .. QDOT_DOUBLE),
+                        QDOT_ZERO for a block without a nonzero component;
+                        item units: 255 (the per-component classes go to `cls`
+                        of qdot_trace) */
+  uint8_t source;    /* QDOT_TRACE_* */
+  uint16_t reserved;
+} qdot_trace_unit;
+
+enum {
+  QDOT_TRACE_NONE = 0,             /* nothing added: perforated or empty block */
+  QDOT_TRACE_SLOT0 = 1,            /* the block's first kept candidate (streaming kernel) */
+  QDOT_TRACE_SLOT1 = 2,            /* its second kept candidate */
+  QDOT_TRACE_SLOT3 = 3,            /* its third kept candidate (HALF, early items) */
+  QDOT_TRACE_RECOMPUTED = 4,       /* the candidate was not kept; recomputed from x, y */
+  QDOT_TRACE_FUSED = 5,            /* the fused kernel's candidate of the block's class */
+  QDOT_TRACE_ITEM = 6,             /* the item's record, accepted */
+  QDOT_TRACE_ITEM_RECOMPUTED = 7   /* the item recomputed with the final classes */
+};
+
+/* Number of qdot_trace_unit records qdot_trace() writes for these arguments,
+ * with the components per unit in *unit_components (B or 256); 0 when qdot()
+ * takes the two-pass path (whose per-component view is qdot_explain) or on
+ * invalid parameters.  `aligned16` tells whether x and y are 16-byte aligned. */
+int64_t qdot_trace_units(int64_t n, const qdot_params* p, int32_t aligned16, int32_t* unit_components);
+
+/* qdot() on the fused or one-pass path, exactly as qdot() runs it (same
+ * kernels, launch shapes and result), that also reports what its kernels
+ * decided, for checking the timed path component by component against an
+ * independent implementation of Algorithm 3.
+ *   units     device array of at least qdot_trace_units(...) records: per
+ *             unit its class (block units) and the exact value the final sum
+ *             took from it (qdot_trace_unit).
+ *   cls       optional device array of n bytes (item units only): the class
+ *             each component was summed with (QDOT_ZERO for zero components);
+ *             left untouched on block paths.  NULL to skip.
+ *   units_len length of `units` in records.
+ * Everything else as for qdot().  Returns QDOT_ERR_ARG when qdot() would take
+ * the two-pass path or `units` is too short. */
+qdot_status qdot_trace(const double* x, const double* y, int64_t n, const qdot_params* p, qdot_result* out,
+                       qdot_trace_unit* units, int64_t units_len, uint8_t* cls, void* ws, size_t ws_bytes,
+                       void* stream);
 
 /* Number of kernels one qdot() call with these arguments launches (0 on
  * invalid parameters); `aligned16` tells whether x and y are 16-byte aligned. */

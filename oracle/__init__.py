@@ -33,8 +33,11 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "qdot_oracle.h")))
     if force or stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
-                       check=True)
+        base = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        # OpenMP only spreads the CPU-baseline helpers over host threads; without
+        # it they run on one thread and every result is the same
+        if subprocess.run(base + ["-fopenmp"], capture_output=True).returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -71,6 +74,8 @@ def _load():
         for name in ("orc_dot_exact", "orc_abs_dot_exact"):
             getattr(lib, name).argtypes = [dp, dp, ctypes.c_int64]
             getattr(lib, name).restype = ctypes.c_double
+        lib.orc_unit_sums.argtypes = [dp, dp, ctypes.c_int64, ctypes.POINTER(_Params), ctypes.c_int64, dp, dp]
+        lib.orc_unit_sums.restype = ctypes.c_int
         lib.orc_sum_exact.argtypes = [dp, ctypes.c_int64]
         lib.orc_sum_exact.restype = ctypes.c_double
         lib.orc_spmv.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, dp, dp, dp]
@@ -83,6 +88,13 @@ def _load():
                                   ctypes.c_double, ctypes.POINTER(_Params), dp, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.c_void_p]
         lib.orc_power.restype = ctypes.c_int
+        lib.orc_qdot_threads.argtypes = [dp, dp, ctypes.c_int64, ctypes.POINTER(_Params), ctypes.c_int,
+                                         ctypes.POINTER(_Result)]
+        lib.orc_qdot_threads.restype = ctypes.c_int
+        lib.orc_dot_fp64.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_int]
+        lib.orc_dot_fp64.restype = ctypes.c_double
+        lib.orc_max_threads.argtypes = []
+        lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_backward.argtypes = [dp, dp, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, dp, dp]
         lib.orc_backward.restype = None
         _lib = lib
@@ -144,6 +156,52 @@ def qdot(x, y, eps: float = 1e-16, block: int = 0, split_budget: int = 1, mant_r
     return OracleResult(res.value, res.value_ld, tuple(res.class_sum), res.bound_elem, res.bound_bins,
                         res.bound_apriori, res.e_max, res.e_min, res.n_bins, res.f, st, tuple(res.count),
                         cls, qx, qy)
+
+
+def unit_sums(x, y, unit: int, eps: float = 1e-16, block: int = 0, split_budget: int = 1, mant_reading: int = 0):
+    """Algorithm 1's partial sums over the index ranges [k*unit, (k+1)*unit):
+    per range the exact sum of q(x_i) q(y_i) (classes of Algorithm 2 on the
+    whole vectors) and the exact sum of |x_i y_i|, each rounded once.
+    Returns (sums, abs_sums) as float64 arrays of ceil(n / unit)."""
+    lib = _load()
+    x = _f64(x)
+    y = _f64(y)
+    n = x.shape[0]
+    m = (n + unit - 1) // unit
+    sums = np.zeros(max(m, 1))
+    abss = np.zeros(max(m, 1))
+    prm = _params(eps, block, split_budget, mant_reading)
+    st = lib.orc_unit_sums(_dp(x), _dp(y), n, ctypes.byref(prm), int(unit), _dp(sums), _dp(abss))
+    if st != 0:
+        raise ValueError(f"oracle status {st}")
+    return sums[:m], abss[:m]
+
+
+def qdot_threads(x, y, eps: float = 1e-16, block: int = 0, split_budget: int = 1, mant_reading: int = 0,
+                 threads: int = 0) -> OracleResult:
+    """qdot with the components split over host threads (CPU baseline): the
+    same value, counts and statistics as ``qdot``; bound fields are 0."""
+    lib = _load()
+    x = _f64(x)
+    y = _f64(y)
+    res = _Result()
+    prm = _params(eps, block, split_budget, mant_reading)
+    nt = threads or lib.orc_max_threads()
+    st = lib.orc_qdot_threads(_dp(x), _dp(y), x.shape[0], ctypes.byref(prm), int(nt), ctypes.byref(res))
+    return OracleResult(res.value, res.value_ld, tuple(res.class_sum), res.bound_elem, res.bound_bins,
+                        res.bound_apriori, res.e_max, res.e_min, res.n_bins, res.f, st, tuple(res.count))
+
+
+def dot_fp64(x, y, threads: int = 1) -> float:
+    """Plain FP64 dot on the host: one fused multiply-add chain per thread."""
+    x = _f64(x)
+    y = _f64(y)
+    return _load().orc_dot_fp64(_dp(x), _dp(y), x.shape[0], int(threads))
+
+
+def max_threads() -> int:
+    """Host threads the threaded helpers use by default (1 without OpenMP)."""
+    return int(_load().orc_max_threads())
 
 
 def quantize(v: float, cls: int) -> float:

@@ -14,7 +14,7 @@
  *
  * Readings of the paper taken here (each one is listed in the design notes):
  *  - exponent of a component: the unbiased IEEE exponent ilogb(v)
- *    (Sec. 1.1 says flexp is the unbiased exponent; Sec. 3.3 extracts it by
+ *    (Sec. 1.1 says flexp is the unbiased exponent; Sec. 3.2 extracts it by
  *    bitmask), subnormals with their true exponent;
  *  - component key e_i = ilogb(x_i) + ilogb(y_i) (Algorithm 2, exponent
  *    preprocessing); a component with x_i = 0 or y_i = 0 is class ZERO:
@@ -40,6 +40,10 @@
 #include <string.h>
 
 #include "qdot_oracle.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------- */
 /* Exact fixed-point accumulator.  Word 0 bit 0 has weight 2^KLSB.  Two's      */
@@ -433,6 +437,47 @@ int orc_qdot(const double* x, const double* y, int64_t n, const orc_params* prm,
   return ORC_OK;
 }
 
+/* Partial sums of Algorithm 1 over index ranges: for every range
+ * [k*unit, (k+1)*unit) of the components, the exact sum of the quantized
+ * products q(x_i) q(y_i) of its components (classes from Algorithm 2 on the
+ * whole vectors, as orc_qdot assigns them) and the exact sum of |x_i y_i|,
+ * each rounded once.  sums and abs_sums hold ceil(n / unit) doubles.
+ * Returns the status of orc_qdot. */
+int orc_unit_sums(const double* x, const double* y, int64_t n, const orc_params* prm, int64_t unit, double* sums,
+                  double* abs_sums) {
+  if (unit < 1) return ORC_ERR_ARG;
+  uint8_t* cls = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
+  orc_result r;
+  int st = orc_qdot(x, y, n, prm, cls, NULL, NULL, &r);
+  if (st != ORC_OK) {
+    free(cls);
+    return st;
+  }
+  for (int64_t lo = 0; lo < n; lo += unit) {
+    kacc q, a;
+    kacc_zero(&q);
+    kacc_zero(&a);
+    for (int64_t i = lo; i < n && i < lo + unit; ++i) {
+      if (cls[i] == ORC_ZERO) continue;
+      uint64_t Mx, My, Mqx, Mqy;
+      int Ex, Ey, Eqx, Eqy;
+      decompose(x[i], &Mx, &Ex);
+      decompose(y[i], &My, &Ey);
+      int neg = (x[i] < 0) != (y[i] < 0);
+      kacc_add(&a, (unsigned __int128)Mx * My, Ex + Ey, 0);
+      if (cls[i] == ORC_PERF) continue;
+      int p = class_bits(cls[i]);
+      round_significand(Mx, Ex, p, &Mqx, &Eqx);
+      round_significand(My, Ey, p, &Mqy, &Eqy);
+      kacc_add(&q, (unsigned __int128)Mqx * Mqy, Eqx + Eqy, neg);
+    }
+    sums[lo / unit] = kacc_to_double(&q);
+    abs_sums[lo / unit] = kacc_to_double(&a);
+  }
+  free(cls);
+  return ORC_OK;
+}
+
 /* Exact x.y rounded once (every component at input precision). */
 double orc_dot_exact(const double* x, const double* y, int64_t n) {
   kacc a;
@@ -584,4 +629,204 @@ void orc_backward(const double* x, const double* y, const uint8_t* cls, int64_t 
     gx[i] = g * orc_quantize(y[i], cls[i]);
     gy[i] = g * orc_quantize(x[i], cls[i]);
   }
+}
+
+/* ------------------------------------------------------------------------- */
+/* CPU baseline: the same computation spread over host threads, and a plain  */
+/* FP64 dot.  Used only to time the host cores; the pins check that the      */
+/* threaded result equals orc_qdot's exactly.                                */
+/* ------------------------------------------------------------------------- */
+
+/* a += b, both exact accumulators (two's complement words with carry). */
+static void kacc_merge(kacc* a, const kacc* b) {
+  uint64_t carry = 0;
+  for (int j = 0; j < KW; ++j) {
+    uint64_t s = a->w[j] + b->w[j];
+    uint64_t c1 = s < b->w[j];
+    uint64_t s2 = s + carry;
+    uint64_t c2 = s2 < carry;
+    a->w[j] = s2;
+    carry = c1 | c2;
+  }
+}
+
+static int key_of(double a, double b) { return ilogb(a) + ilogb(b); }
+
+/* orc_qdot's value, counts and statistics with the components split over
+ * nthreads host threads (OpenMP when built with it): Algorithm 2's
+ * statistics per thread, then merged; Algorithm 1's exact sum per thread in
+ * its own accumulator, the accumulators added exactly, one rounding.  The
+ * bound fields of res are left 0. */
+int orc_qdot_threads(const double* x, const double* y, int64_t n, const orc_params* prm, int nthreads,
+                     orc_result* res) {
+  memset(res, 0, sizeof(*res));
+  if (n < 0 || !(prm->eps > 0.0) || !isfinite(prm->eps) || prm->block < 0 || nthreads < 1) {
+    res->status = ORC_ERR_ARG;
+    return ORC_ERR_ARG;
+  }
+  const int m_half = prm->mant_reading ? 11 : 10;
+  const int m_single = prm->mant_reading ? 24 : 23;
+  enum { KMIN = -2148, KCOUNT = 4224 };
+  int bad = 0, e_max = INT32_MIN, e_min = INT32_MAX;
+  int64_t nonzero = 0;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) reduction(| : bad) reduction(max : e_max) reduction(min : e_min) \
+    reduction(+ : nonzero) schedule(static)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    if (!isfinite(x[i]) || !isfinite(y[i])) {
+      bad |= 1;
+      continue;
+    }
+    if (x[i] == 0.0 || y[i] == 0.0) continue;
+    const int e = key_of(x[i], y[i]);
+    if (e > e_max) e_max = e;
+    if (e < e_min) e_min = e;
+    nonzero++;
+  }
+  if (bad) {
+    res->status = ORC_ERR_NONFINITE;
+    return ORC_ERR_NONFINITE;
+  }
+  if (nonzero == 0) e_max = e_min = 0;
+  /* bins: per block (u_b, M_b), or per key (count) */
+  int64_t n_bins = 0;
+  const int64_t B = prm->block;
+  const int64_t nblk = B > 0 ? (n + B - 1) / B : 0;
+  int32_t* bu = NULL;
+  int64_t* bm = NULL;
+  int64_t hist[KCOUNT];
+  memset(hist, 0, sizeof(hist));
+  if (B > 0) {
+    bu = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nblk > 0 ? nblk : 1));
+    bm = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nblk > 0 ? nblk : 1));
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) reduction(+ : n_bins) schedule(static)
+#endif
+    for (int64_t b = 0; b < nblk; ++b) {
+      int32_t u = INT32_MIN;
+      int64_t m = 0;
+      for (int64_t i = b * B; i < n && i < (b + 1) * B; ++i) {
+        if (x[i] == 0.0 || y[i] == 0.0) continue;
+        const int e = key_of(x[i], y[i]);
+        if (e > u) u = e;
+        m++;
+      }
+      bu[b] = u;
+      bm[b] = m;
+      n_bins += m > 0;
+    }
+  } else {
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+      int64_t h[KCOUNT];
+      memset(h, 0, sizeof(h));
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+      for (int64_t i = 0; i < n; ++i)
+        if (x[i] != 0.0 && y[i] != 0.0) h[key_of(x[i], y[i]) - KMIN] += 1;
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+      for (int k = 0; k < KCOUNT; ++k) hist[k] += h[k];
+    }
+    for (int k = 0; k < KCOUNT; ++k) n_bins += hist[k] > 0;
+  }
+  const int32_t f = n_bins > 0 ? orc_floor_log2_ratio(prm->eps, prm->split_budget ? n_bins : 1) : 0;
+  /* Algorithm 1 per thread */
+  kacc* accs = (kacc*)malloc(sizeof(kacc) * (size_t)nthreads);
+  int64_t counts[5] = {0, 0, 0, 0, 0};
+  int64_t* tcounts = (int64_t*)calloc((size_t)nthreads * 5, sizeof(int64_t));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    kacc_zero(&accs[t]);
+    int64_t* c = tcounts + 5 * t;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+      if (x[i] == 0.0 || y[i] == 0.0) {
+        c[ORC_ZERO] += 1;
+        continue;
+      }
+      int64_t sigma;
+      if (B > 0) {
+        const int64_t b = i / B;
+        sigma = (int64_t)ceil_log2_u64((uint64_t)bm[b]) + bu[b] - e_max - f + 1;
+      } else {
+        const int e = key_of(x[i], y[i]);
+        sigma = (int64_t)ceil_log2_u64((uint64_t)hist[e - KMIN]) + e - e_max - f + 1;
+      }
+      const int cls = precision_of_score(sigma, m_half, m_single);
+      c[cls] += 1;
+      if (cls == ORC_PERF) continue;
+      uint64_t Mx, My, Mqx, Mqy;
+      int Ex, Ey, Eqx, Eqy;
+      decompose(x[i], &Mx, &Ex);
+      decompose(y[i], &My, &Ey);
+      const int p = class_bits(cls);
+      round_significand(Mx, Ex, p, &Mqx, &Eqx);
+      round_significand(My, Ey, p, &Mqy, &Eqy);
+      kacc_add(&accs[t], (unsigned __int128)Mqx * Mqy, Eqx + Eqy, (x[i] < 0) != (y[i] < 0));
+    }
+  }
+  for (int t = 1; t < nthreads; ++t) kacc_merge(&accs[0], &accs[t]);
+  for (int t = 0; t < nthreads; ++t)
+    for (int k = 0; k < 5; ++k) counts[k] += tcounts[5 * t + k];
+  res->value = kacc_to_double(&accs[0]);
+  res->e_max = e_max;
+  res->e_min = e_min;
+  res->n_bins = n_bins;
+  res->f = f;
+  res->status = ORC_OK;
+  for (int k = 0; k < 5; ++k) res->count[k] = counts[k];
+  free(accs);
+  free(tcounts);
+  free(bu);
+  free(bm);
+  return ORC_OK;
+}
+
+/* Plain FP64 dot product x.y on nthreads host threads: each thread one
+ * fused multiply-add chain over its contiguous share, the thread sums added
+ * in thread order (the CPU counterpart of the GPU comparator). */
+double orc_dot_fp64(const double* x, const double* y, int64_t n, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  double* part = (double*)calloc((size_t)nthreads, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+  {
+    int t = 0, nt = 1;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+    nt = omp_get_num_threads();
+#endif
+    const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+    double s = 0.0;
+    for (int64_t i = lo; i < hi; ++i) s = fma(x[i], y[i], s);
+    part[t] = s;
+  }
+  double s = 0.0;
+  for (int t = 0; t < nthreads; ++t) s += part[t];
+  free(part);
+  return s;
+}
+
+/* Threads the OpenMP runtime would use (1 without OpenMP). */
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

@@ -36,6 +36,8 @@ int orc_qdot(const double* x, const double* y, int64_t n, const orc_params* prm,
              double* qx_out, double* qy_out, orc_result* res);
 double orc_quantize(double v, int cls);
 int orc_floor_log2_ratio(double eps, int64_t N);
+int orc_unit_sums(const double* x, const double* y, int64_t n, const orc_params* prm, int64_t unit, double* sums,
+                  double* abs_sums);
 double orc_dot_exact(const double* x, const double* y, int64_t n);
 double orc_abs_dot_exact(const double* x, const double* y, int64_t n);
 double orc_sum_exact(const double* v, int64_t n);
@@ -46,6 +48,10 @@ int orc_cg(int64_t n, const int64_t* rowptr, const int32_t* col, const double* v
            int64_t* class_counts);
 int orc_power(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, double* x, int32_t iters,
               double tau, const orc_params* prm, double* lambda, int32_t* done_iters, int64_t* class_counts);
+int orc_qdot_threads(const double* x, const double* y, int64_t n, const orc_params* prm, int nthreads,
+                     orc_result* res);
+double orc_dot_fp64(const double* x, const double* y, int64_t n, int nthreads);
+int orc_max_threads(void);
 void orc_backward(const double* x, const double* y, const uint8_t* cls, int64_t n, double g, double* gx,
                   double* gy);
 

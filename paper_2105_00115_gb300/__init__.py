@@ -13,9 +13,10 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _abi
-from ._abi import Params, QdotError, Result, Selection, check, load
+from ._abi import Params, QdotError, Result, Selection, TraceUnit, check, load
 
-__all__ = ["QdotResult", "QdotError", "qdot", "qdot_async", "explain", "dot_fp64", "from_host", "workspace_size",
+__all__ = ["QdotResult", "QdotError", "qdot", "qdot_async", "explain", "trace", "dot_fp64", "from_host",
+           "workspace_size",
            "load", "params", "decode_result", "Batch", "Csr", "cg", "cg_batched", "power"]
 
 CLASS_NAMES = ("perforate", "half", "single", "double", "zero")
@@ -137,6 +138,45 @@ def explain(x, y, eps=1e-16, block=32, split_budget=1, mant_reading=0, stream=No
                           _ptr(ws), ws.numel(), _stream_ptr(stream))
     check(st, lib)
     return decode_result(out.cpu().numpy()), cls, qx, qy
+
+
+TRACE_DTYPE = np.dtype([("value", "<i8"), ("grid", "<i4"), ("cls", "u1"), ("source", "u1"), ("reserved", "<u2")])
+
+
+def trace(x, y, eps=1e-16, block=32, split_budget=1, mant_reading=0, path="auto", want_cls=True, stream=None):
+    """qdot on the fused or one-pass path, exactly as ``qdot`` runs it, plus
+    what its kernels decided: returns (result, units, unit_components, cls).
+
+    ``units`` is a numpy record array (value, grid, cls, source) with one
+    record per block (or per warp item of 256 components on the item-record
+    paths): the unit contributed value * 2**grid to the sum.  ``cls`` is the
+    per-component class map (uint8 CUDA tensor) on item-record paths (when
+    ``want_cls``), else None.  Raises QdotError when the arguments take the
+    two-pass path."""
+    torch = _torch()
+    lib = load()
+    _check_vec(x, "x")
+    _check_vec(y, "y")
+    if x.numel() != y.numel():
+        raise ValueError("x and y must have the same length")
+    p = params(eps, block, split_budget, mant_reading, path)
+    n = x.numel()
+    al16 = int((x.data_ptr() | y.data_ptr()) % 16 == 0)
+    per = ctypes.c_int32(0)
+    nunits = int(lib.qdot_trace_units(n, ctypes.byref(p), al16, ctypes.byref(per)))
+    if nunits == 0 and n > 0:
+        raise QdotError(1, "these arguments take the two-pass path (use explain)")
+    ws = _workspace(lib.qdot_workspace_size(n, ctypes.byref(p)), x.device)
+    out = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=x.device)
+    units = torch.zeros(max(nunits, 1) * ctypes.sizeof(TraceUnit), dtype=torch.uint8, device=x.device)
+    cls = None
+    if want_cls and lib.qdot_stream_kernel(n, ctypes.byref(p), al16) == b"k_onepass_items":  # item records
+        cls = torch.full((n,), 255, dtype=torch.uint8, device=x.device)
+    st = lib.qdot_trace(_ptr(x), _ptr(y), n, ctypes.byref(p), _ptr(out), _ptr(units), nunits, _ptr(cls), _ptr(ws),
+                        ws.numel(), _stream_ptr(stream))
+    check(st, lib)
+    rec = units.cpu().numpy().view(TRACE_DTYPE)[:nunits]
+    return decode_result(out.cpu().numpy()), rec, per.value, cls
 
 
 def dot_fp64(x, y, stream=None) -> float:

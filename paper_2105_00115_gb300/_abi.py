@@ -32,6 +32,16 @@ class Selection(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 2), ("cls", ctypes.c_uint8 * KEY_COUNT)]
 
 
+class TraceUnit(ctypes.Structure):
+    _fields_ = [("value", ctypes.c_int64), ("grid", ctypes.c_int32), ("cls", ctypes.c_uint8),
+                ("source", ctypes.c_uint8), ("reserved", ctypes.c_uint16)]
+
+
+# qdot_trace_unit sources (include/qdot.h)
+TRACE_SOURCES = {0: "none", 1: "slot0", 2: "slot1", 3: "slot3", 4: "recomputed", 5: "fused", 6: "item",
+                 7: "item_recomputed"}
+
+
 class Csr(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
                 ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
@@ -56,6 +66,7 @@ assert ctypes.sizeof(Result) == 80
 assert ctypes.sizeof(CgInfo) == 64
 assert ctypes.sizeof(PowerInfo) == 56
 assert ctypes.sizeof(Params) == 24
+assert ctypes.sizeof(TraceUnit) == 16
 
 # (name, restype, argtypes) for every entry point of include/qdot.h
 _VP = ctypes.c_void_p
@@ -84,6 +95,8 @@ SIGNATURES = {
     "qdot_dot_fp64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     "qdot_from_host": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "qdot_static_scratch": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP]),
+    "qdot_trace_units": (_I64, [_I64, _PP, _I32, _VP]),
+    "qdot_trace": (ctypes.c_int, [_VP, _VP, _I64, _PP, _VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
     "qdot_kernel_launches": (_I32, [_I64, _PP, _I32]),
     "qdot_select_path": (_I32, [_I64, _PP, _I32]),
     "qdot_stream_kernel": (ctypes.c_char_p, [_I64, _PP, _I32]),

@@ -254,6 +254,50 @@ qdot_status qdot_explain(const double* x, const double* y, int64_t n, const qdot
   return QDOT_OK;
 }
 
+int64_t qdot_trace_units(int64_t n, const qdot_params* p, int32_t al16, int32_t* unit_components) {
+  std::string why;
+  if (unit_components) *unit_components = 0;
+  if (!valid_params(n, p, &why)) return 0;
+  const PathChoice c = choose_path(n, p, al16 != 0);
+  if (c == kTwoPass) return 0;
+  const bool items = c == kOnePass && plan_one_pass(n, p).items;
+  const int64_t per = items ? 256 : p->block;
+  if (unit_components) *unit_components = (int32_t)per;
+  return (n + per - 1) / per;
+}
+
+qdot_status qdot_trace(const double* x, const double* y, int64_t n, const qdot_params* p, qdot_result* out,
+                       qdot_trace_unit* units, int64_t units_len, uint8_t* cls, void* ws, size_t ws_bytes,
+                       void* stream) {
+  clear_error();
+  qdot_status s = check_common(x, y, n, p, out, ws);
+  if (s != QDOT_OK) return s;
+  const bool al16 = aligned16(x, y);
+  PathChoice c;
+  const size_t need = workspace_for(n, p, al16, &c);
+  if (ws_bytes < need) {
+    set_error("qdot_trace: workspace too small (" + std::to_string(ws_bytes) + " < " + std::to_string(need) + ")");
+    return QDOT_ERR_WORKSPACE;
+  }
+  if (c == kTwoPass) {
+    set_error("qdot_trace: these arguments take the two-pass path; its per-component view is qdot_explain");
+    return QDOT_ERR_ARG;
+  }
+  const int64_t need_units = qdot_trace_units(n, p, al16 ? 1 : 0, nullptr);
+  if (n > 0 && (!units || units_len < need_units)) {
+    set_error("qdot_trace: units must hold " + std::to_string(need_units) + " records");
+    return QDOT_ERR_ARG;
+  }
+  TraceOut tr;
+  tr.units = units;
+  tr.cls = cls;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = c == kFused ? launch_fused(x, y, n, p, ws, out, nullptr, st, tr)
+                                    : launch_one_pass(x, y, n, p, plan_one_pass(n, p), ws, out, nullptr, st, tr);
+  if (e != cudaSuccess) return cuda_fail("qdot_trace launch", e);
+  return QDOT_OK;
+}
+
 size_t qdot_dot_fp64_workspace_size(void) { return dot_fp64_workspace(); }
 
 qdot_status qdot_dot_fp64(const double* x, const double* y, int64_t n, double* out, void* ws, size_t ws_bytes,

@@ -312,20 +312,62 @@ __device__ __forceinline__ void acc_fast_mask(unsigned mask, const Chunk& ch, co
   }
 }
 
-// Per-lane variant of acc_fast for the single-call stream: each lane's block
-// has its own primary class `prim` (its highest wanted candidate), computed on
-// the FP64 pipe with that lane's rounding: SINGLE lanes round both operands to
-// 24 bits, HALF lanes to 11 bits, DOUBLE lanes (and lanes with no candidate)
+// Candidates of the single-call paths (one-pass, fused) and of their
+// recomputations share ONE definition, whatever route computes them, so a
+// result does not depend on which candidates a speculation kept:
+//   C_b(c) = sum over the lanes of block b of trunc(A_lane(c) * 2^G_c),
+//   A_lane(c) = fl(fma(r_c(x^_7), r_c(y^_7), ... fma(r_c(x^_0), r_c(y^_0), 0))),
+// the fused multiply-adds taken over the lane's nonzero components in the
+// order j = 0..7 of the streaming layout, with
+//   x^_j = sign(x) 1.m_x (the significand of x, exponent field 1023),
+//   y^_j = sign(y) 1.m_y 2^-min(d_j, 1022), d_j = u_b - e_j,
+// r_c the rounding of the significand to 11 (HALF) or 24 (SINGLE) bits, ties
+// to even (a carry moves into the exponent field), r_D the identity, and
+// G_H = G_D = 60 - log2 B, G_S = 52 (grids 2^(u_b - 60 + log2 B) and 2^(u_b - 52)).
+// HALF and SINGLE products of rounded operands are exact in FP64; the lane
+// sums of at most 8 terms below 4 each stay below 2^5, so every truncated lane
+// value fits in 64 bits with room for the sum over a block's lanes.
+
+// The chain operands of a finite nonzero pair (x, y), d = u_b - e (>= 0).
+__device__ __forceinline__ void chain_operands(uint64_t xb, uint64_t yb, int d, uint64_t& xo, uint64_t& yo) {
+  constexpr uint64_t kFrac = 0x000FFFFFFFFFFFFFull, kSign = 0x8000000000000000ull;
+  xo = (xb & kSign) | 0x3FF0000000000000ull | (significand_of(xb) & kFrac);
+  yo = (yb & kSign) | ((uint64_t)(1023 - min(d, 1022)) << 52) | (significand_of(yb) & kFrac);
+}
+
+// One fused multiply-add of the chain of class cls (kHalf, kSingle, kDouble).
+__device__ __forceinline__ double chain_step(uint64_t xo, uint64_t yo, int cls, double a) {
+  if (cls == kHalf) {
+    xo = round_bits<42>(xo);
+    yo = round_bits<42>(yo);
+  } else if (cls == kSingle) {
+    xo = round_bits<29>(xo);
+    yo = round_bits<29>(yo);
+  }
+  return fma(__longlong_as_double((long long)xo), __longlong_as_double((long long)yo), a);
+}
+
+// Scale of the grid of class cls relative to 2^u_b (2^G_c above).
+template <int LOG2B>
+__device__ __forceinline__ double chain_scale(int cls) {
+  return cls == kSingle ? 4503599627370496.0 : (double)(1ll << (60 - LOG2B));  // 2^52, 2^(60 - log2 B)
+}
+
+// Per-lane variant for the single-call stream: each lane's block has its own
+// primary class `prim` (its highest wanted candidate), computed on the FP64
+// pipe with that lane's rounding: SINGLE lanes round both operands to 24
+// bits, HALF lanes to 11 bits, DOUBLE lanes (and lanes with no candidate)
 // keep them.  RMODE (warp-uniform) has bit 0 set when some lane is SINGLE,
 // bit 1 when some lane is HALF.  The SINGLE rounding uses per-lane constants
-// that leave the other lanes' operands unchanged; the HALF rounding is a
-// branch (HALF lanes are usually few, next to perforated ones).  IMASK (warp-uniform) names
-// the secondary classes some block wants besides its primary; they take the
-// integer path in every lane, and each block keeps only its own.
+// that leave the other lanes' operands unchanged (the same bits as
+// round_bits<29>); the HALF rounding is a branch (HALF lanes are usually few,
+// next to perforated ones).  IMASK (warp-uniform) names the secondary classes
+// some block wants besides its primary; they take chains of their own in
+// every lane (aH2, aS2), and each block keeps only its own.  Every chain is
+// the one defined above.
 template <int LOG2B, int RMODE, unsigned IMASK>
-__device__ __forceinline__ void acc_lane(const Chunk& ch, const int (&key)[8], int u, unsigned prim, long long& aH,
-                                         long long& aS, double& aF) {
-  constexpr int K = LOG2B;
+__device__ __forceinline__ void acc_lane(const Chunk& ch, const int (&key)[8], int u, unsigned prim, double& aH2,
+                                         double& aS2, double& aF) {
   const bool rs = prim == kCandS, rh = prim == kCandH;
   // SINGLE: round to nearest even at bit 29 of the 64-bit pattern
   const uint32_t s_inc = rs ? 0x0FFFFFFFu : 0u;    // half an ulp less one
@@ -336,21 +378,11 @@ __device__ __forceinline__ void acc_lane(const Chunk& ch, const int (&key)[8], i
     const uint32_t hx = (uint32_t)(ch.x[j] >> 32), lx = (uint32_t)ch.x[j];
     const uint32_t hy = (uint32_t)(ch.y[j] >> 32), ly = (uint32_t)ch.y[j];
     const int d = u - key[j];
-    if (IMASK) {
-      const uint32_t mx = (hx & 0xFFFFFu) | 0x100000u, my = (hy & 0xFFFFFu) | 0x100000u;
-      const int sgn = product_sign(hx, hy);
-      if (IMASK & kCandH) {
-        const int yh = (int)half_sig(my, ly) * sgn;
-        aH += sar64((long long)((int)half_sig(mx, lx) * yh) << (40 - K), d);
-      }
-      if (IMASK & kCandS) {
-        const int ys = (int)single_sig(my, ly) * (sgn * 64);
-        aS += sar64((long long)(int)single_sig(mx, lx) * (long long)ys, d);
-      }
-    }
     const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
     uint64_t xo = ((uint64_t)((hx & 0x800FFFFFu) | 0x3FF00000u) << 32) | lx;
     uint64_t yo = ((uint64_t)((hy & 0x800FFFFFu) | ye) << 32) | ly;
+    if (IMASK & kCandH) aH2 = chain_step(xo, yo, kHalf, aH2);
+    if (IMASK & kCandS) aS2 = chain_step(xo, yo, kSingle, aS2);
     if (RMODE & 1) {  // a carry out of the fraction moves into the exponent field
       xo = (xo + (s_inc + (((uint32_t)xo >> 29) & s_bit))) & (0xFFFFFFFF00000000ull | s_mask);
       yo = (yo + (s_inc + (((uint32_t)yo >> 29) & s_bit))) & (0xFFFFFFFF00000000ull | s_mask);
@@ -365,25 +397,61 @@ __device__ __forceinline__ void acc_lane(const Chunk& ch, const int (&key)[8], i
 
 template <int LOG2B, int RMODE>
 __device__ __forceinline__ void acc_lane_i(unsigned imask, const Chunk& ch, const int (&key)[8], int u, unsigned prim,
-                                           long long& aH, long long& aS, double& aF) {
+                                           double& aH2, double& aS2, double& aF) {
   switch (imask >> 1) {  // warp-uniform
-    case 0: acc_lane<LOG2B, RMODE, 0u>(ch, key, u, prim, aH, aS, aF); break;
-    case 1: acc_lane<LOG2B, RMODE, kCandH>(ch, key, u, prim, aH, aS, aF); break;
-    case 2: acc_lane<LOG2B, RMODE, kCandS>(ch, key, u, prim, aH, aS, aF); break;
-    default: acc_lane<LOG2B, RMODE, kCandH | kCandS>(ch, key, u, prim, aH, aS, aF); break;
+    case 0: acc_lane<LOG2B, RMODE, 0u>(ch, key, u, prim, aH2, aS2, aF); break;
+    case 1: acc_lane<LOG2B, RMODE, kCandH>(ch, key, u, prim, aH2, aS2, aF); break;
+    case 2: acc_lane<LOG2B, RMODE, kCandS>(ch, key, u, prim, aH2, aS2, aF); break;
+    default: acc_lane<LOG2B, RMODE, kCandH | kCandS>(ch, key, u, prim, aH2, aS2, aF); break;
   }
 }
 
 // rounds: the primaries of the warp's lanes (OR); imask: their secondaries (OR).
 template <int LOG2B>
 __device__ __forceinline__ void acc_lane_mask(unsigned rounds, unsigned imask, const Chunk& ch, const int (&key)[8],
-                                              int u, unsigned prim, long long& aH, long long& aS, double& aF) {
+                                              int u, unsigned prim, double& aH2, double& aS2, double& aF) {
   switch (((rounds & kCandS) ? 1 : 0) | ((rounds & kCandH) ? 2 : 0)) {  // warp-uniform
-    case 0: acc_lane_i<LOG2B, 0>(imask, ch, key, u, prim, aH, aS, aF); break;
-    case 1: acc_lane_i<LOG2B, 1>(imask, ch, key, u, prim, aH, aS, aF); break;
-    case 2: acc_lane_i<LOG2B, 2>(imask, ch, key, u, prim, aH, aS, aF); break;
-    default: acc_lane_i<LOG2B, 3>(imask, ch, key, u, prim, aH, aS, aF); break;
+    case 0: acc_lane_i<LOG2B, 0>(imask, ch, key, u, prim, aH2, aS2, aF); break;
+    case 1: acc_lane_i<LOG2B, 1>(imask, ch, key, u, prim, aH2, aS2, aF); break;
+    case 2: acc_lane_i<LOG2B, 2>(imask, ch, key, u, prim, aH2, aS2, aF); break;
+    default: acc_lane_i<LOG2B, 3>(imask, ch, key, u, prim, aH2, aS2, aF); break;
   }
+}
+
+// Any component (zeros, subnormals, non-finite values, past the end) on the
+// chains defined above: the lane's chains of the classes in MASK, the block
+// maximum key (biased; kNone if the block has no nonzero component)
+// returned, the lane's counts added.
+template <int LOG2B, unsigned MASK = kCandAll>
+__device__ __forceinline__ int chunk_general_chains(const Chunk& ch, double& aH, double& aS, double& aD, int& M,
+                                                    int& zeros, int& kmin, int& bad) {
+  int key[8];
+  bool nz[8];
+  int cmax = kNone;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t a = ch.x[j], b = ch.y[j];
+    const bool in = (ch.vmask >> j) & 1u;
+    const bool fin = !(is_nonfinite(a) || is_nonfinite(b));
+    bad |= in && !fin;
+    const bool z = is_zero(a) || is_zero(b);
+    nz[j] = in && fin && !z;
+    zeros += in && fin && z;
+    M += nz[j];
+    key[j] = nz[j] ? exponent_of(a) + exponent_of(b) + 2046 : kNone;  // biased like the fast path
+    cmax = max(cmax, key[j]);
+    if (nz[j]) kmin = min(kmin, key[j]);
+  }
+  const int u = group_max<Map<LOG2B>::L>(cmax);
+  for (int j = 0; j < 8; ++j) {
+    if (!nz[j]) continue;
+    uint64_t xo, yo;
+    chain_operands(ch.x[j], ch.y[j], u - key[j], xo, yo);
+    if (MASK & kCandH) aH = chain_step(xo, yo, kHalf, aH);
+    if (MASK & kCandS) aS = chain_step(xo, yo, kSingle, aS);
+    if (MASK & kCandD) aD = chain_step(xo, yo, kDouble, aD);
+  }
+  return u;
 }
 
 // Candidates of one component with key e (biased) in a block with maximum
@@ -484,40 +552,32 @@ __device__ __forceinline__ long long block_record_word(long long aH, long long a
 // u_b = s_b - ceil(log2 M_b).
 constexpr int kMetaKeyBias = 4096;
 
-// aF holds the candidate of class `top` (kCand*): D or H on the grid
-// 2^(u - 60 + K), S on 2^(u - 52).
+// Record of a general block (single-call stream): aH, aS, aD are the lane's
+// chains of every class (chunk_general_chains), moved to their grids here.
 template <int LOG2B>
-__device__ __forceinline__ void block_record_compact(long long aH, long long aS, double aF, unsigned top, int M,
-                                                     int u_b, unsigned stored, int sub, int* key_out, int* u_out,
-                                                     int* m_out, long long* slot, unsigned* meta,
-                                                     long long* half_out) {
+__device__ __forceinline__ void block_record_compact(double aH, double aS, double aD, int M, int u_b,
+                                                     unsigned stored, int sub, int* key_out, int* u_out, int* m_out,
+                                                     long long* slot, unsigned* meta, long long* half_out) {
   constexpr int L = Map<LOG2B>::L;
-  long long aDi = 0;
-  if (top == kCandS)
-    aS = __double2ll_rz(aF * 4503599627370496.0);  // 2^52
-  else if (top == kCandH)
-    aH = __double2ll_rz(aF * (double)(1ll << (60 - LOG2B)));
-  else
-    aDi = __double2ll_rz(aF * (double)(1ll << (60 - LOG2B)));
-  aH = group_sum<L>(aH);
-  aS = group_sum<L>(aS);
-  aDi = group_sum<L>(aDi);
+  const long long h = group_sum<L>(__double2ll_rz(aH * chain_scale<LOG2B>(kHalf)));
+  const long long s = group_sum<L>(__double2ll_rz(aS * chain_scale<LOG2B>(kSingle)));
+  const long long d = group_sum<L>(__double2ll_rz(aD * chain_scale<LOG2B>(kDouble)));
   M = group_sum_i<L>(M);
   const int u = u_b - 2046;
   const int key = M > 0 ? ceil_log2_u32((uint32_t)M) + u : (int)kEmptyKey;
   *key_out = key;
   *u_out = u;
   *m_out = M;
-  *half_out = aH;
+  *half_out = h;
   long long hi, lo;
   if (stored & kCandD) {
-    hi = aDi;
-    lo = (stored & kCandS) ? aS : aH;
+    hi = d;
+    lo = (stored & kCandS) ? s : h;
   } else if (stored & kCandS) {
-    hi = aS;
-    lo = aH;
+    hi = s;
+    lo = h;
   } else {
-    hi = aH;
+    hi = h;
     lo = 0;
   }
   *slot = sub == 0 ? hi : lo;
@@ -528,19 +588,18 @@ __device__ __forceinline__ void block_record_compact(long long aH, long long aS,
 
 // Compact record of a plain block (B nonzero components, M_b = B): every lane
 // of the block holds the same primary class `prim` in aF, so one group sum
-// covers it; the secondaries (classes in `imask`, warp-uniform) are summed
-// only when some block of the warp keeps one.
+// covers it; the secondaries (chains aH2, aS2 of the classes in `imask`,
+// warp-uniform) are summed only when some block of the warp keeps one.
 template <int LOG2B>
-__device__ __forceinline__ void block_record_plain(long long aH, long long aS, double aF, unsigned prim,
-                                                   unsigned imask, int u_b, unsigned stored, int sub, int* u_out,
-                                                   long long* slot, unsigned* meta, long long* half_out) {
+__device__ __forceinline__ void block_record_plain(double aH2, double aS2, double aF, unsigned prim, unsigned imask,
+                                                   int u_b, unsigned stored, int sub, int* u_out, long long* slot,
+                                                   unsigned* meta, long long* half_out) {
   constexpr int L = Map<LOG2B>::L;
-  const long long hi =
-      group_sum<L>(__double2ll_rz(aF * (prim == kCandS ? 4503599627370496.0 : (double)(1ll << (60 - LOG2B)))));
-  long long lo = 0, h = 0;
-  if (imask & kCandH) h = group_sum<L>(aH);
-  if (imask & kCandS) aS = group_sum<L>(aS);
-  if (stored & ~prim & kCandS) lo = aS;
+  const long long hi = group_sum<L>(__double2ll_rz(aF * chain_scale<LOG2B>(prim == kCandS ? kSingle : kDouble)));
+  long long lo = 0, h = 0, s = 0;
+  if (imask & kCandH) h = group_sum<L>(__double2ll_rz(aH2 * chain_scale<LOG2B>(kHalf)));
+  if (imask & kCandS) s = group_sum<L>(__double2ll_rz(aS2 * chain_scale<LOG2B>(kSingle)));
+  if (stored & ~prim & kCandS) lo = s;
   else if (stored & ~prim & kCandH) lo = h;
   const int u = u_b - 2046;
   *u_out = u;
@@ -579,7 +638,9 @@ __device__ __forceinline__ i128 record_candidate(long long h, long long s, long 
 }
 
 // The candidate of class cls of block blk, recomputed from x and y at the
-// record's grid (u unbiased): used when the streaming kernel skipped it.
+// record's grid (u unbiased), as the batched stream forms its candidates
+// (HALF and SINGLE products truncated to the grid one by one, DOUBLE on one
+// chain): used by the batched finisher when the stream skipped it.
 template <int LOG2B>
 __device__ long long recompute_candidate(const double* __restrict__ x, const double* __restrict__ y, long long n,
                                          long long blk, int u, int cls) {
@@ -615,6 +676,50 @@ __device__ long long recompute_candidate_warp(const double* __restrict__ x, cons
     component_candidates<LOG2B>(a, b, e, u + 2046, mask, aH, aS, aD);
   }
   long long v = cls == kHalf ? aH : (cls == kSingle ? aS : __double2ll_rz(aD * (double)(1ll << (60 - LOG2B))));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Lane `sub` of block blk (0 <= sub < B / 8) recomputed on its chain of
+// class cls (the definition above; u the block maximum, unbiased): the same
+// components, in the same order, as in the streaming layout.  Returns the
+// lane's truncated value on the class grid.
+template <int LOG2B>
+__device__ __forceinline__ long long recompute_chain_lane(const double* __restrict__ x, const double* __restrict__ y,
+                                                          long long n, long long blk, int u, int cls, int sub) {
+  constexpr int L = Map<LOG2B>::L;
+  const long long base = (blk << LOG2B) + 2 * sub;
+  double a = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const long long i = base + 2 * L * (j >> 1) + (j & 1);
+    if (i >= n) continue;
+    const uint64_t xb = (uint64_t)__double_as_longlong(x[i]), yb = (uint64_t)__double_as_longlong(y[i]);
+    if (is_zero(xb) || is_zero(yb)) continue;
+    uint64_t xo, yo;
+    chain_operands(xb, yb, u - (exponent_of(xb) + exponent_of(yb)), xo, yo);
+    a = chain_step(xo, yo, cls, a);
+  }
+  return __double2ll_rz(a * chain_scale<LOG2B>(cls));
+}
+
+// The candidate of class cls of block blk by one thread (every lane's chain
+// in turn) ...
+template <int LOG2B>
+__device__ long long recompute_chain(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                     long long blk, int u, int cls) {
+  long long v = 0;
+  for (int sub = 0; sub < Map<LOG2B>::L; ++sub) v += recompute_chain_lane<LOG2B>(x, y, n, blk, u, cls, sub);
+  return v;
+}
+
+// ... or by one warp (lane l < B / 8 takes chain l).  Every lane returns the
+// total; both give the value the streaming kernel gives.
+template <int LOG2B>
+__device__ long long recompute_chain_warp(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                          long long blk, int u, int cls, int lane) {
+  long long v = lane < Map<LOG2B>::L ? recompute_chain_lane<LOG2B>(x, y, n, blk, u, cls, lane) : 0ll;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;

@@ -19,7 +19,7 @@ typedef __int128 i128;
 typedef unsigned __int128 u128;
 
 // ---------------------------------------------------------------------------
-// Component decoding (Sec. 1.1 flexp = unbiased exponent; Sec. 3.3 bitmask).
+// Component decoding (Sec. 1.1 flexp = unbiased exponent; Sec. 3.2 bitmask).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ bool is_nonfinite(uint64_t bits) {

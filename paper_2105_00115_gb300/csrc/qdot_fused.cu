@@ -4,16 +4,22 @@
 // At these sizes the multi-kernel paths spend most of their time in launch
 // gaps and one-CTA kernels.  Here one cooperative launch does everything:
 //   phase 1  every warp streams its items (at most kFusedItems) and keeps, per
-//            block, the exact HALF / SINGLE / DOUBLE candidates, the block
-//            key and M_b in shared memory (blocked binning, 32 <= B <= 256);
-//            per-CTA statistics go to the workspace;
+//            block, the DOUBLE candidate, the block key and M_b in shared
+//            memory (blocked binning, 32 <= B <= 256); per-CTA statistics go
+//            to the workspace;
 //   sync     grid-wide barrier;
 //   phase 2  every CTA reduces the statistics (e_max, N_bins, f exactly), then
-//            classes its own blocks (eq. bin-score-def, eq. precision-def) and
-//            sums their chosen candidates exactly;
+//            classes its own blocks (eq. bin-score-def, eq. precision-def):
+//            a DOUBLE block adds its kept candidate, a HALF or SINGLE block is
+//            summed again from x and y (held in L2 at these sizes) on the
+//            chain of its class, a perforated block adds nothing; all of it
+//            exactly, in fixed point.  When e_max - e_min <= -f - m_single
+//            every block is DOUBLE (Theorem 5), so no class is looked up and
+//            nothing is read again;
 //   phase 3  the last CTA to finish phase 2 (an arrival counter) adds the
 //            per-CTA sums in order and rounds once.
-// The values are those of the one-pass path (same candidates and grids).
+// Every candidate is the one-pass path's (qdot_chunk.cuh: one chain per lane
+// of the streaming layout), so both paths return the same bits.
 #include <climits>
 #include <cooperative_groups.h>
 
@@ -32,8 +38,8 @@ constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kFusedItems = 8;    // items per warp at most
 constexpr int kFusedCtasPerSm = 1;
 
-struct FusedBlock {  // one block's candidates (in shared memory)
-  long long h, s, d;
+struct FusedBlock {  // one block's DOUBLE candidate (in shared memory)
+  long long d;
   int key;           // s_b, kEmptyKey when the block has no nonzero component
   unsigned m;        // M_b
 };
@@ -52,7 +58,8 @@ template <int LOG2B>
 __global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm)
     k_qdot_fused(const double* __restrict__ x, const double* __restrict__ y, long long n, qdot_params prm,
                  CtaStats* __restrict__ cstats, FusedPart* __restrict__ parts, unsigned* __restrict__ arrivals,
-                 qdot_selection* __restrict__ sel, qdot_result* __restrict__ out) {
+                 qdot_selection* __restrict__ sel, qdot_result* __restrict__ out,
+                 qdot_trace_unit* __restrict__ trace) {
   constexpr int L = Map<LOG2B>::L, BPI = Map<LOG2B>::BPI;
   __shared__ FusedBlock s_blk[kFusedWarps][kFusedItems][BPI];
   __shared__ CtaStats s_w[kFusedWarps];
@@ -78,25 +85,21 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm)
   if (gwarp < nitems) load_item<LOG2B>(x, y, n, gwarp, lane, cur);
   for (long long it = gwarp; it < nitems && k < kFusedItems; it += nwarps, ++k) {
     if (it + nwarps < nitems) load_item<LOG2B>(x, y, n, it + nwarps, lane, nxt);
-    long long aH = 0, aS = 0;
-    double aD = 0.0;
+    double aH = 0.0, aS = 0.0, aD = 0.0;
     int M = 0, zeros = 0, u;
     int key[8];
     int cmax = kNone;
     if (__all_sync(0xffffffffu, chunk_keys(cur, key, cmax, kmin))) {
       u = group_max<L>(cmax);
       M = 8;
-      acc_fast<LOG2B, kCandAll>(cur, key, u, aH, aS, aD);
+      acc_lane<LOG2B, 0, 0u>(cur, key, u, kCandD, aH, aS, aD);  // the DOUBLE chain
     } else {
-      u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);
+      u = chunk_general_chains<LOG2B, kCandD>(cur, aH, aS, aD, M, zeros, kmin, bad);
     }
     int kb, ub, mb;
-    long long hv = 0, sv = 0, dv = 0;
+    long long dv = 0;
     {
-      long long aDi = __double2ll_rz(aD * (double)(1ll << (60 - LOG2B)));
-      hv = group_sum<L>(aH);
-      sv = group_sum<L>(aS);
-      dv = group_sum<L>(aDi);
+      dv = group_sum<L>(__double2ll_rz(aD * chain_scale<LOG2B>(kDouble)));
       mb = group_sum_i<L>(M);
       ub = u - 2046;
       kb = mb > 0 ? ceil_log2_u32((uint32_t)mb) + ub : (int)kEmptyKey;
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm)
       nbins += (sub == 0);
       emax_l = max(emax_l, ub);
     }
-    if (sub == 0) s_blk[w][k][g] = FusedBlock{hv, sv, dv, real ? kb : (int)kEmptyKey, (unsigned)mb};
+    if (sub == 0) s_blk[w][k][g] = FusedBlock{dv, real ? kb : (int)kEmptyKey, (unsigned)mb};
     cur = nxt;
   }
   emax_l = __reduce_max_sync(0xffffffffu, emax_l);
@@ -177,15 +180,31 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm)
   const int lsb = e_max - fixed_point_bits(n);
   i128 acc = 0;
   unsigned long long cnt[4] = {0, 0, 0, 0};
-  if (!s_bad && sub == 0) {
-    for (int kk = 0; kk < k; ++kk) {
+  // Theorem 5: every score is at least m_single, so every block is DOUBLE
+  const bool all_double = (long long)e_max - s_emin <= -(long long)f - ms;
+  if (!s_bad) {
+    for (int kk = 0; kk < k; ++kk) {  // k is the same in every lane of the warp
       const FusedBlock b = s_blk[w][kk][g];
-      if (b.key == (int)kEmptyKey) continue;
-      const int cls = precision_of((long long)b.key - e_max - f + 1, mh, ms);
+      const long long blk = (gwarp + kk * nwarps) * BPI + g;
+      const bool empty = b.key == (int)kEmptyKey;
+      const int cls = empty ? kZero : (all_double ? kDouble : precision_of((long long)b.key - e_max - f + 1, mh, ms));
+      const int u = empty ? 0 : b.key - ceil_log2_u32(b.m);
+      // HALF and SINGLE blocks: every lane of the block sums its chain again
+      // (no shuffle inside the branch), then the block's lanes add up
+      long long lv = 0;
+      if (cls == kHalf || cls == kSingle) lv = recompute_chain_lane<LOG2B>(x, y, n, blk, u, cls, sub);
+      if (!all_double) lv = group_sum<L>(lv);
+      if (sub == 0 && !empty) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) cnt[c] += (cls == c) ? b.m : 0u;
-      const int u = b.key - ceil_log2_u32(b.m);
-      acc += record_candidate(b.h, b.s, b.d, u, cls, LOG2B, lsb);
+        for (int c = 0; c < 4; ++c) cnt[c] += (cls == c) ? b.m : 0u;
+        const long long v = cls == kDouble ? b.d : lv;
+        if (cls != kPerf) acc += candidate_to_fixed(v, cls, u, LOG2B, lsb);
+        if (trace)  // check output only (qdot_trace)
+          trace[blk] = qdot_trace_unit{cls != kPerf ? v : 0ll, cls != kPerf ? candidate_grid(cls, u, LOG2B) : 0,
+                                       (uint8_t)cls, (uint8_t)(cls != kPerf ? QDOT_TRACE_FUSED : QDOT_TRACE_NONE), 0};
+      }
+      if (sub == 0 && empty && trace && blk < nblocks)
+        trace[blk] = qdot_trace_unit{0ll, 0, (uint8_t)kZero, (uint8_t)QDOT_TRACE_NONE, 0};
     }
   }
   acc = warp_sum_i128(acc);
@@ -288,7 +307,7 @@ int fused_grid() {
 
 template <int LOG2B>
 cudaError_t launch_fused_lb(const double* x, const double* y, int64_t n, const qdot_params* p, char* ws,
-                            qdot_result* out, qdot_selection* sel, cudaStream_t st) {
+                            qdot_result* out, qdot_selection* sel, cudaStream_t st, qdot_trace_unit* trace) {
   const int grid = fused_grid<LOG2B>();
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   auto* cstats = reinterpret_cast<CtaStats*>(ws);
@@ -297,8 +316,8 @@ cudaError_t launch_fused_lb(const double* x, const double* y, int64_t n, const q
                                                align_up(sizeof(FusedPart) * (size_t)grid, 256));
   long long nn = n;
   qdot_params prm = *p;
-  void* args[] = {(void*)&x,     (void*)&y,        (void*)&nn,  (void*)&prm, (void*)&cstats,
-                  (void*)&parts, (void*)&arrivals, (void*)&sel, (void*)&out};
+  void* args[] = {(void*)&x,        (void*)&y,   (void*)&nn,  (void*)&prm,  (void*)&cstats, (void*)&parts,
+                  (void*)&arrivals, (void*)&sel, (void*)&out, (void*)&trace};
   cudaEvent_t ev0, ev1;
   kernel_events(&ev0, &ev1);
   if (ev0) cudaEventRecord(ev0, st);
@@ -336,15 +355,15 @@ size_t fused_ws_bytes() {
 }
 
 cudaError_t launch_fused(const double* x, const double* y, int64_t n, const qdot_params* p, void* ws,
-                         qdot_result* out, qdot_selection* sel, cudaStream_t st) {
+                         qdot_result* out, qdot_selection* sel, cudaStream_t st, TraceOut tr) {
   char* w = static_cast<char*>(ws);
   int lb = 0;
   while ((1 << lb) < p->block) ++lb;
   switch (lb) {
-    case 5: return launch_fused_lb<5>(x, y, n, p, w, out, sel, st);
-    case 6: return launch_fused_lb<6>(x, y, n, p, w, out, sel, st);
-    case 7: return launch_fused_lb<7>(x, y, n, p, w, out, sel, st);
-    default: return launch_fused_lb<8>(x, y, n, p, w, out, sel, st);
+    case 5: return launch_fused_lb<5>(x, y, n, p, w, out, sel, st, tr.units);
+    case 6: return launch_fused_lb<6>(x, y, n, p, w, out, sel, st, tr.units);
+    case 7: return launch_fused_lb<7>(x, y, n, p, w, out, sel, st, tr.units);
+    default: return launch_fused_lb<8>(x, y, n, p, w, out, sel, st, tr.units);
   }
 }
 

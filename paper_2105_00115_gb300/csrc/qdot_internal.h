@@ -28,6 +28,12 @@ const DeviceInfo& device_info();
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Optional check outputs of qdot_trace(); both null on the timed path.
+struct TraceOut {
+  qdot_trace_unit* units = nullptr;  // per block or per item
+  uint8_t* cls = nullptr;            // per component (item paths)
+};
+
 // Execution modes of the two-pass path.
 enum Mode { kModeExact = 0, kModeBlock1 = 1, kModeBlockSmall = 2, kModeBlockLarge = 3 };
 
@@ -70,14 +76,14 @@ const char* one_pass_stream_kernel(int64_t n, const qdot_params* p);
 int one_pass_launches(int64_t n, const qdot_params* p);
 cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const qdot_params* p,
                             const OnePassPlan& plan, void* ws, qdot_result* out, qdot_selection* sel,
-                            cudaStream_t stream);
+                            cudaStream_t stream, TraceOut trace = TraceOut());
 
 // One-launch qdot for vectors the resident grid covers in a few items
 // (cooperative launch with grid-wide barriers).
 bool fused_supported(int64_t n, const qdot_params* p, bool aligned16);
 size_t fused_ws_bytes();
 cudaError_t launch_fused(const double* x, const double* y, int64_t n, const qdot_params* p, void* ws,
-                         qdot_result* out, qdot_selection* sel, cudaStream_t stream);
+                         qdot_result* out, qdot_selection* sel, cudaStream_t stream, TraceOut trace = TraceOut());
 
 // qdot() on device buffers with the path qdot() would choose (no checks);
 // ws must hold qdot_workspace_size(n, p) bytes.

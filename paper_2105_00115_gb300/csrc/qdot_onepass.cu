@@ -208,8 +208,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
     cp_async_wait<kStages - 1>();  // this lane's copies of item `it` have landed
     read_item<LOG2B>(ring + stage * kStageWords, n, it, lane, cur);
     stage = stage == kStages - 1 ? 0 : stage + 1;
-    long long aH = 0, aS = 0;
-    double aD = 0.0;
+    double aH = 0.0, aS = 0.0, aD = 0.0;  // the lane's chains (see qdot_chunk.cuh)
     int M = 0, zeros = 0, u;
     unsigned want = 0;
     int key[8];
@@ -227,10 +226,10 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass(const doub
       block_record_plain<LOG2B>(aH, aS, aD, prim, imask, u, want, sub, &ub, &slot, &meta, &half);
       mb = 1 << LOG2B;
     } else {
-      u = chunk_general<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);  // every candidate
+      u = chunk_general_chains<LOG2B>(cur, aH, aS, aD, M, zeros, kmin, bad);  // every candidate
       want = candidates_wanted<LOG2B>(u, lane, iter, early_items, f_spec, mh, ms, erun, e_lo, pending, raised);
       int kb;
-      block_record_compact<LOG2B>(aH, aS, aD, kCandD, M, u, want, sub, &kb, &ub, &mb, &slot, &meta, &half);
+      block_record_compact<LOG2B>(aH, aS, aD, M, u, want, sub, &kb, &ub, &mb, &slot, &meta, &half);
     }
     // the record keeps the block's wanted candidates
     const long long blk = it * BPI + g;
@@ -440,7 +439,8 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
                                                    long long nblocks, qdot_selection* __restrict__ sel,
                                                    OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
                                                    const double* __restrict__ x, const double* __restrict__ y,
-                                                   long long n, qdot_result* __restrict__ out) {
+                                                   long long n, qdot_result* __restrict__ out,
+                                                   qdot_trace_unit* __restrict__ trace) {
   __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
   __shared__ long long s_qblk[kRepairQueue];  // blocks to recompute ...
   __shared__ int s_qinfo[kRepairQueue];       // ... with u << 2 | class
@@ -467,23 +467,32 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
     const int top = 31 - __clz((int)(stored | 1u));  // the highest kept class sits in slot 0
     long long v = sl0;
     bool keep = cls != kPerf;
+    int src = keep ? QDOT_TRACE_SLOT0 : QDOT_TRACE_NONE;
     if (keep && cls != top) {  // a second kept candidate, or a missing one
       if (stored == kCandAll && cls == kHalf && blk >= n_early) stored = 0;  // never written
       if (stored & (1u << cls)) {
-        v = (stored == kCandAll && cls == kHalf) ? slot3[blk]  // blk < n_early by construction
-                                                 : slots1[blk];
+        const bool third = stored == kCandAll && cls == kHalf;
+        v = third ? slot3[blk]  // blk < n_early by construction
+                  : slots1[blk];
+        src = third ? QDOT_TRACE_SLOT3 : QDOT_TRACE_SLOT1;
       } else {
         ++c_rep;
         keep = false;
+        src = QDOT_TRACE_RECOMPUTED;
         const int q = atomicAdd(&s_nqueue, 1);
         if (q < kRepairQueue) {  // the CTA's warps recompute it together after the sweep
           s_qblk[q] = blk;
           s_qinfo[q] = (u << 2) | cls;
         } else {  // queue full: this thread recomputes it alone
-          acc += candidate_to_fixed(recompute_candidate<LOG2B>(x, y, n, blk, u, cls), cls, u, LOG2B, lsb);
+          const long long rv = recompute_chain<LOG2B>(x, y, n, blk, u, cls);
+          acc += candidate_to_fixed(rv, cls, u, LOG2B, lsb);
+          if (trace) trace[blk] = qdot_trace_unit{rv, candidate_grid(cls, u, LOG2B), (uint8_t)cls, (uint8_t)src, 0};
         }
       }
     }
+    if (trace && src != QDOT_TRACE_RECOMPUTED)
+      trace[blk] = qdot_trace_unit{keep ? v : 0ll, keep ? candidate_grid(cls, u, LOG2B) : 0,
+                                   (uint8_t)(mw ? cls : kZero), (uint8_t)src, 0};
     // v on its grid 2^g, moved to 2^lsb: g - lsb <= L - 52 <= 52 (u <= e_max, L <= 104);
     // a negative shift truncates, as the fixed-point sum does
     const int sh = candidate_grid(cls, u, LOG2B) - lsb;
@@ -521,8 +530,12 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
   for (int qi = w; qi < nq; qi += (int)(blockDim.x >> 5)) {
     const long long blk = s_qblk[qi];
     const int cls = s_qinfo[qi] & 3, u = s_qinfo[qi] >> 2;
-    const long long v = recompute_candidate_warp<LOG2B>(x, y, n, blk, u, cls, lane);
-    if (lane == 0) acc += candidate_to_fixed(v, cls, u, LOG2B, lsb);
+    const long long v = recompute_chain_warp<LOG2B>(x, y, n, blk, u, cls, lane);
+    if (lane == 0) {
+      acc += candidate_to_fixed(v, cls, u, LOG2B, lsb);
+      if (trace)
+        trace[blk] = qdot_trace_unit{v, candidate_grid(cls, u, LOG2B), (uint8_t)cls, (uint8_t)QDOT_TRACE_RECOMPUTED, 0};
+    }
   }
   acc += (i128)(((unsigned __int128)(unsigned long long)acc_hi << 64) | acc_lo);
   unsigned long long c[5] = {c_ph & 0xFFFFFFFFull, c_ph >> 32, c_sd & 0xFFFFFFFFull, c_sd >> 32, c_rep};
@@ -595,7 +608,8 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
                                                                  int f_spec, int mh, int ms, int* __restrict__ erun,
                                                                  WarpStats* __restrict__ wstats,
                                                                  long long* __restrict__ isum,
-                                                                 unsigned long long* __restrict__ imeta) {
+                                                                 unsigned long long* __restrict__ imeta,
+                                                                 uint8_t* __restrict__ tcls) {
   constexpr int LB = LOG2B ? LOG2B : 8;  // the item layout (blocks of one: that of 256)
   constexpr int L = Map<LB>::L;
   const int lane = threadIdx.x & 31;
@@ -650,14 +664,22 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
         seen = __reduce_or_sync(0xffffffffu, seen);
         const unsigned rmode = ((seen >> kSingle) & 1u) | (((seen >> kHalf) & 1u) << 1) | ((seen & 1u) << 2);
         acc_components_mode(rmode, cur, key, u, cls, aF);
+        if (tcls) {  // check output only (qdot_trace)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tcls[it * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls[j];
+        }
       } else {
         const int sg = LB + group_max<L>(cmax) - a;  // the block's score (M_b = B)
         const int cls = sg < 0 ? kPerf : (sg < mh ? kHalf : (sg < ms ? kSingle : kDouble));
         const unsigned prim = cls == kPerf ? 0u : 1u << cls;
-        long long aH = 0, aS = 0;
-        acc_lane_mask<LB>(__reduce_or_sync(0xffffffffu, prim), 0u, cur, key, u, prim, aH, aS, aF);
+        double aH2 = 0.0, aS2 = 0.0;
+        acc_lane_mask<LB>(__reduce_or_sync(0xffffffffu, prim), 0u, cur, key, u, prim, aH2, aS2, aF);
         if (!prim) aF = 0.0;  // a perforated block adds nothing
         cnt = 8u << (cls << 3);
+        if (tcls) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tcls[it * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls;
+        }
       }
       long long v = __double2ll_rz(aF * 4503599627370496.0);  // onto the grid 2^(u - 52)
 #pragma unroll
@@ -721,60 +743,60 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
   }
 }
 
-// One item recomputed by a warp with the final classes: lane l takes the
-// components item*256 + l + 32k (coalesced), so slice k lies in block
-// (l + 32k) >> LOG2B of the item.  Returns the item's sum on the grid
-// 2^(u - 52) (u its largest key, unbiased, in *u_out; kNone if the item has
-// no nonzero component) and adds the lane's class counts to c.
+// One item recomputed by a warp with the final classes, on the streaming
+// layout and the chains of the streaming kernel (any components: zeros,
+// subnormals, the vectors' end).  Returns the item's sum on the grid
+// 2^(u - 52) (u its largest key, unbiased, in *u_out; kNone if the item has no
+// nonzero component), adds the lane's class counts to c and, when tcls is
+// given (qdot_trace), writes each component's class.
 template <int LOG2B>
 __device__ long long recompute_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
                                     long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
-                                    unsigned long long (&c)[5]) {
-  uint64_t xa[8], ya[8];
-  int e[8];
-  int u = kNone;
+                                    unsigned long long (&c)[5], uint8_t* __restrict__ tcls) {
+  constexpr int LB = LOG2B ? LOG2B : 8;  // the item layout (blocks of one: that of 256)
+  constexpr int L = Map<LB>::L;
+  Chunk ch;
+  load_item<LB>(x, y, n, item, lane, ch);
+  int key[8];
+  bool nz[8];
+  int cmax = kNone, m = 0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const long long i = item * kItem + lane + 32 * k;
-    xa[k] = i < n ? (uint64_t)__double_as_longlong(x[i]) : 0ull;
-    ya[k] = i < n ? (uint64_t)__double_as_longlong(y[i]) : 0ull;
-    const bool use = !(is_zero(xa[k]) || is_zero(ya[k]) || is_nonfinite(xa[k]) || is_nonfinite(ya[k]));
-    e[k] = use ? exponent_of(xa[k]) + exponent_of(ya[k]) : kNone;
-    u = max(u, e[k]);
+  for (int j = 0; j < 8; ++j) {
+    const uint64_t a = ch.x[j], b = ch.y[j];
+    nz[j] = ((ch.vmask >> j) & 1u) && !(is_zero(a) || is_zero(b) || is_nonfinite(a) || is_nonfinite(b));
+    key[j] = nz[j] ? exponent_of(a) + exponent_of(b) + 2046 : kNone;  // biased
+    cmax = max(cmax, key[j]);
+    m += nz[j];
   }
-  u = __reduce_max_sync(0xffffffffu, u);
-  *u_out = u;
-  if (u == kNone) return 0;
+  const int u = __reduce_max_sync(0xffffffffu, cmax);
   int cls[8];
   if (LOG2B == 0) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) cls[k] = e[k] == kNone ? kPerf : lut[e[k] - kKeyMin];
-  } else {
-    constexpr int KPB = (1 << LOG2B) / 32;  // slices per block
+    for (int j = 0; j < 8; ++j) cls[j] = nz[j] ? (int)lut[key[j] - 2046 - kKeyMin] : kZero;
+  } else {  // the block key s_b = ceil(log2 M_b) + u_b over the block's L lanes
+    const int ub = group_max<L>(cmax), mb = group_sum_i<L>(m);
+    const int cb = mb ? (int)lut[ceil_log2_u32((uint32_t)mb) + ub - 2046 - kKeyMin] : kPerf;
 #pragma unroll
-    for (int b = 0; b < 8 / KPB; ++b) {
-      int ub = kNone, mb = 0;
-#pragma unroll
-      for (int kk = 0; kk < KPB; ++kk) {
-        const int k = b * KPB + kk;
-        ub = max(ub, __reduce_max_sync(0xffffffffu, e[k]));
-        mb += __popc(__ballot_sync(0xffffffffu, e[k] != kNone));
-      }
-      const int cb = mb ? lut[ceil_log2_u32((uint32_t)mb) + ub - kKeyMin] : kPerf;  // the block key s_b
-#pragma unroll
-      for (int kk = 0; kk < KPB; ++kk) cls[b * KPB + kk] = cb;
-    }
+    for (int j = 0; j < 8; ++j) cls[j] = nz[j] ? cb : kZero;
   }
-  long long aH = 0, aS = 0;
-  double aD = 0.0;
+  if (tcls) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (e[k] == kNone) continue;
-    c[cls[k]] += 1;
-    if (cls[k] != kPerf)
-      component_candidates<8>(xa[k], ya[k], e[k] + 2046, u + 2046, 1u << cls[k], aH, aS, aD);
+    for (int j = 0; j < 8; ++j)
+      if ((ch.vmask >> j) & 1u) tcls[item * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls[j];
   }
-  long long v = aH + aS + __double2ll_rz(aD * 4503599627370496.0);
+  *u_out = u == kNone ? kNone : u - 2046;
+  if (u == kNone) return 0;  // warp-uniform
+  double a = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (!nz[j]) continue;
+    c[cls[j]] += 1;
+    if (cls[j] == kPerf) continue;
+    uint64_t xo, yo;
+    chain_operands(ch.x[j], ch.y[j], u - key[j], xo, yo);
+    a = chain_step(xo, yo, cls[j], a);
+  }
+  long long v = __double2ll_rz(a * 4503599627370496.0);  // grid 2^(u - 52)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -788,7 +810,7 @@ __device__ long long recompute_item(const double* __restrict__ x, const double* 
 template <int LOG2B>
 __device__ long long recompute_item_fast(const double* __restrict__ x, const double* __restrict__ y, long long n,
                                          long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
-                                         unsigned long long (&c)[5]) {
+                                         unsigned long long (&c)[5], uint8_t* __restrict__ tcls) {
   constexpr int LB = LOG2B ? LOG2B : 8;
   constexpr int L = Map<LB>::L;
   Chunk ch;
@@ -796,7 +818,7 @@ __device__ long long recompute_item_fast(const double* __restrict__ x, const dou
   int key[8];
   int cmax = kNone, kmin = INT_MAX;
   if (!__all_sync(0xffffffffu, chunk_keys(ch, key, cmax, kmin)))
-    return recompute_item<LOG2B>(x, y, n, item, lut, lane, u_out, c);
+    return recompute_item<LOG2B>(x, y, n, item, lut, lane, u_out, c, tcls);
   const int u = __reduce_max_sync(0xffffffffu, cmax);  // biased
   *u_out = u - 2046;
   double aF = 0.0;
@@ -812,13 +834,21 @@ __device__ long long recompute_item_fast(const double* __restrict__ x, const dou
     seen = __reduce_or_sync(0xffffffffu, seen);
     acc_components_mode(((seen >> kSingle) & 1u) | (((seen >> kHalf) & 1u) << 1) | ((seen & 1u) << 2), ch, key, u,
                         cls, aF);
+    if (tcls) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) tcls[item * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls[j];
+    }
   } else {
     const int cls = lut[LB + group_max<L>(cmax) - 2046 - kKeyMin];  // the block key s_b = log2 B + u_b
     c[cls] += 8;
     const unsigned prim = cls == kPerf ? 0u : 1u << cls;
-    long long aH = 0, aS = 0;
-    acc_lane_mask<LB>(__reduce_or_sync(0xffffffffu, prim), 0u, ch, key, u, prim, aH, aS, aF);
+    double aH2 = 0.0, aS2 = 0.0;
+    acc_lane_mask<LB>(__reduce_or_sync(0xffffffffu, prim), 0u, ch, key, u, prim, aH2, aS2, aF);
     if (!prim) aF = 0.0;
+    if (tcls) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) tcls[item * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls;
+    }
   }
   long long v = __double2ll_rz(aF * 4503599627370496.0);  // grid 2^(u - 52)
 #pragma unroll
@@ -838,7 +868,8 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
                                                      int f_spec, qdot_selection* __restrict__ sel,
                                                      OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
                                                      const double* __restrict__ x, const double* __restrict__ y,
-                                                     long long n, qdot_result* __restrict__ out) {
+                                                     long long n, qdot_result* __restrict__ out,
+                                                     qdot_trace_unit* __restrict__ trace, uint8_t* __restrict__ tcls) {
   __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
   __shared__ long long s_qitem[256];
   __shared__ int s_nqueue;
@@ -874,6 +905,7 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
         const unsigned long long lo = (unsigned long long)wv << sl;
         acc_lo += lo;
         acc_hi += ((wv >> 1) >> (63 - sl)) + (acc_lo < lo ? 1 : 0);
+        if (trace) trace[i] = qdot_trace_unit{v, (int)(m & 0xFFFu) - 2046 - 52, 255, (uint8_t)QDOT_TRACE_ITEM, 0};
       } else {
         ++c[4];
         s_qitem[atomicAdd(&s_nqueue, 1)] = i;  // at most one per thread and round
@@ -883,8 +915,11 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
     const int nq = s_nqueue;
     for (int qi = w; qi < nq; qi += (int)(blockDim.x >> 5)) {
       int u;
-      const long long v = recompute_item_fast<LOG2B>(x, y, n, s_qitem[qi], s_lut, lane, &u, c);
+      const long long v = recompute_item_fast<LOG2B>(x, y, n, s_qitem[qi], s_lut, lane, &u, c, tcls);
       if (lane == 0 && u != kNone) acc += candidate_to_fixed(v, kSingle, u, 8, lsb);  // grid 2^(u - 52)
+      if (lane == 0 && trace)
+        trace[s_qitem[qi]] = qdot_trace_unit{u != kNone ? v : 0ll, u != kNone ? u - 52 : 0, 255,
+                                             (uint8_t)QDOT_TRACE_ITEM_RECOMPUTED, 0};
     }
     __syncthreads();
     if (threadIdx.x == 0) s_nqueue = 0;
@@ -906,7 +941,7 @@ int host_floor_log2_ratio(double eps, unsigned long long N) {
 
 template <int LOG2B>
 cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_params* p, const OnePassPlan& pl,
-                      char* ws, qdot_result* out, cudaStream_t st) {
+                      char* ws, qdot_result* out, cudaStream_t st, TraceOut tr) {
   auto* sel = reinterpret_cast<qdot_selection*>(ws + pl.off_sel);
   auto* hdr = reinterpret_cast<OpHeader*>(ws + pl.off_hdr);
   auto* wst = reinterpret_cast<WarpStats*>(ws + pl.off_rec);
@@ -938,13 +973,13 @@ cudaError_t launch_lb(const double* x, const double* y, int64_t n, const qdot_pa
   k_op_select<<<1, 1024, 0, st>>>(wst, nw, n, *p, sel, hdr);
   const int gather_grid = 4 * (device_info().sms > 0 ? device_info().sms : 152);
   k_op_gather<LOG2B><<<gather_grid, 256, 0, st>>>(slots, slots1, metas, slot3, 2ll * pl.grid * kOpWarps * Map<LOG2B>::BPI,
-                                                    nblocks, sel, hdr, parts, x, y, n, out);
+                                                    nblocks, sel, hdr, parts, x, y, n, out, tr.units);
   return cudaGetLastError();
 }
 
 template <int LOG2B>
 cudaError_t launch_items(const double* x, const double* y, int64_t n, const qdot_params* p, const OnePassPlan& pl,
-                         char* ws, qdot_result* out, cudaStream_t st) {
+                         char* ws, qdot_result* out, cudaStream_t st, TraceOut tr) {
   auto* sel = reinterpret_cast<qdot_selection*>(ws + pl.off_sel);
   auto* hdr = reinterpret_cast<OpHeader*>(ws + pl.off_hdr);
   auto* wst = reinterpret_cast<WarpStats*>(ws + pl.off_rec);
@@ -969,12 +1004,12 @@ cudaError_t launch_items(const double* x, const double* y, int64_t n, const qdot
     smem_set = true;
   }
   k_onepass_items<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, isum,
-                                                                 imeta);
+                                                                 imeta, tr.cls);
   if (ev1) cudaEventRecord(ev1, st);
   k_op_select<<<1, 1024, 0, st>>>(wst, pl.grid * kOpWarps, n, *p, sel, hdr);
   const int gather_grid = 2 * (device_info().sms > 0 ? device_info().sms : 152);  // 2 CTAs per SM
   k_op_gather_items<LOG2B><<<gather_grid, 256, 0, st>>>(isum, imeta, nitems, f_spec, sel, hdr, parts, x, y, n,
-                                                         out);
+                                                         out, tr.units, tr.cls);
   return cudaGetLastError();
 }
 
@@ -1031,15 +1066,15 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
 
 cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const qdot_params* p,
                             const OnePassPlan& plan, void* ws, qdot_result* out, qdot_selection* sel,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, TraceOut tr) {
   char* w = static_cast<char*>(ws);
   cudaError_t e;
   switch (plan.log2b) {
-    case 0: e = launch_items<0>(x, y, n, p, plan, w, out, stream); break;
-    case 5: e = plan.items ? launch_items<5>(x, y, n, p, plan, w, out, stream) : launch_lb<5>(x, y, n, p, plan, w, out, stream); break;
-    case 6: e = plan.items ? launch_items<6>(x, y, n, p, plan, w, out, stream) : launch_lb<6>(x, y, n, p, plan, w, out, stream); break;
-    case 7: e = plan.items ? launch_items<7>(x, y, n, p, plan, w, out, stream) : launch_lb<7>(x, y, n, p, plan, w, out, stream); break;
-    default: e = plan.items ? launch_items<8>(x, y, n, p, plan, w, out, stream) : launch_lb<8>(x, y, n, p, plan, w, out, stream); break;
+    case 0: e = launch_items<0>(x, y, n, p, plan, w, out, stream, tr); break;
+    case 5: e = plan.items ? launch_items<5>(x, y, n, p, plan, w, out, stream, tr) : launch_lb<5>(x, y, n, p, plan, w, out, stream, tr); break;
+    case 6: e = plan.items ? launch_items<6>(x, y, n, p, plan, w, out, stream, tr) : launch_lb<6>(x, y, n, p, plan, w, out, stream, tr); break;
+    case 7: e = plan.items ? launch_items<7>(x, y, n, p, plan, w, out, stream, tr) : launch_lb<7>(x, y, n, p, plan, w, out, stream, tr); break;
+    default: e = plan.items ? launch_items<8>(x, y, n, p, plan, w, out, stream, tr) : launch_lb<8>(x, y, n, p, plan, w, out, stream, tr); break;
   }
   if (e != cudaSuccess) return e;
   if (sel) e = cudaMemcpyAsync(sel, w + plan.off_sel, sizeof(qdot_selection), cudaMemcpyDeviceToDevice, stream);

@@ -23,21 +23,58 @@ constexpr size_t kStaticScratchBytes = QDOT_STATIC_SCRATCH_BYTES;
 // device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch on the current device, looked up once per
-// device (with that device current) and cached.
+// Identity of the calling thread's current CUDA context (0 if there is none
+// or the driver cannot tell), through driver entry points the runtime hands
+// out, so the library needs no link to the driver library.  The runtime
+// destroys a device's context on cudaDeviceReset() and makes a new one on
+// the next call; the array's address is only valid in the context it was
+// looked up in.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return 0;
+  unsigned long long id = 0;
+  return get_id(ctx, &id) == 0 ? id : 0;
+}
+
+// Device address of g_static_scratch on the current device, looked up with
+// that device current and cached per device together with the context it
+// belongs to: a call in another context (after a device reset) looks it up
+// again.
 cudaError_t static_scratch_address(void** out) {
   static std::mutex mu;
   static void* addr[64] = {nullptr};
+  static unsigned long long ctx_of[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!addr[dev] || ctx == 0 || ctx != ctx_of[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
     addr[dev] = p;
+    ctx_of[dev] = current_context_id();  // the context the lookup ran in
   }
   *out = addr[dev];
   return cudaSuccess;
@@ -73,7 +110,8 @@ extern "C" qdot_status qdot_static_scratch(const double* x, const double* y, int
   if (plan.total > kStaticScratchBytes) {
     set_error("qdot_static_scratch: these arguments need " + std::to_string(plan.total) +
               " bytes of scratch, more than the library's fixed " + std::to_string(kStaticScratchBytes) +
-              " (large blocks keep 2 bytes per block); use qdot() with a workspace instead");
+              " (blocks of more than 64 components, or of more than 32 with 8-byte aligned x, y, keep 2 bytes "
+              "per block); use qdot() with a workspace instead");
     return QDOT_ERR_WORKSPACE;
   }
   void* ws = nullptr;

@@ -1,0 +1,215 @@
+"""Element-wise parity of the timed kernels (fused, one-pass with block
+records, one-pass with item records) against the CPU oracle, through
+qdot_trace(): the same launches as qdot(), plus what they decided.
+
+For every unit of work (a block of B components, or a warp item of 256):
+- the class the selection gave it (expanded to components; on item paths the
+  per-component class map the kernels summed with) equals the oracle's class
+  map bit for bit;
+- the value the final sum took from it, value * 2^grid, is within
+  unit * 2^-52 * sum_unit |x_i y_i| of the oracle's exact sum of
+  q(x_i) q(y_i) over the same components (the per-lane chain roundings and
+  grid truncations of the kernels, derived in qdot_chunk.cuh, stay below
+  that);
+- a perforated or empty unit adds exactly 0.
+A wrong candidate slot, a stale window or a wrong recomputation changes a
+unit's value by far more than its tolerance, even when the total stays
+within 1e-13 sum |x_i y_i|.
+
+Every candidate has one definition whatever route computes it, so repeated
+calls, and the fused and one-pass paths on the same data, agree bit for bit.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-13
+SRC = {"none": 0, "slot0": 1, "slot1": 2, "slot3": 3, "recomputed": 4, "fused": 5, "item": 6, "item_recomputed": 7}
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_00115_gb300 import build as qbuild
+    qbuild.build()
+    import paper_2105_00115_gb300 as qq
+    qq.load()
+    return qq
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _class_map(units, per, cls, x, y, block):
+    """Per-component classes the kernels used: item paths report them per
+    component; block paths per block (ZERO for the block's zero products)."""
+    if cls is not None:
+        return cls.cpu().numpy()
+    n = x.shape[0]
+    m = np.repeat(units["cls"], per)[:n].copy()
+    m[(x == 0.0) | (y == 0.0)] = 4
+    return m
+
+
+def check_trace(q, orc, x, y, eps, block, path="auto", expect_kernel=None, xd=None, yd=None):
+    """Run qdot_trace and compare it with the oracle unit by unit; returns
+    (result, units) for further checks."""
+    lib = q.load()
+    if xd is None:
+        xd, yd = _dev(x), _dev(y)
+    if expect_kernel is not None:
+        p = q.params(eps, block, 1, 0, path)
+        assert lib.qdot_stream_kernel(x.shape[0], ctypes.byref(p), 1).decode() == expect_kernel
+    r, units, per, cls = q.trace(xd, yd, eps=eps, block=block, path=path)
+    ref = orc.qdot(x, y, eps=eps, block=block, explain=True)
+    assert r.status == 0
+    assert r.count == tuple(ref.count)
+    assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f)
+    assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y)
+    # the class map, bit for bit
+    np.testing.assert_array_equal(_class_map(units, per, cls, x, y, block), ref.cls)
+    # every unit's value against the oracle's exact partial sum
+    sums, abss = orc.unit_sums(x, y, per, eps=eps, block=block)
+    assert len(units) == len(sums)
+    val = np.ldexp(units["value"].astype(np.float64), units["grid"])
+    err = np.abs(val - sums)
+    tol = per * 2.0**-52 * abss + 2.0**-1074
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, (f"{bad.size} units off, first {bad[:5]}: value {val[bad[:5]]} oracle {sums[bad[:5]]} "
+                           f"sources {units['source'][bad[:5]]}")
+    # perforated and empty units add exactly nothing
+    if per == block:
+        none = units["source"] == SRC["none"]
+        assert np.all(np.isin(units["cls"][none], (0, 4)))
+        assert np.all(units["value"][none] == 0)
+    return r, units
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_trace_fused(q, orc, block):
+    """The one-launch path at the solvers' sizes (Theorem 5 fast path included:
+    eps = 1e-15 leaves every block DOUBLE on kind a)."""
+    n = (1 << 21) + 77
+    for kind in ("a", "b", "c"):
+        x, y = workloads.pair(kind, n, 300 + block)
+        xd, yd = _dev(x), _dev(y)
+        for eps in (1e-15, 1e-8, 1e-1):
+            _, units = check_trace(q, orc, x, y, eps, block, expect_kernel="k_qdot_fused", xd=xd, yd=yd)
+            assert np.all(np.isin(units["source"], (SRC["none"], SRC["fused"])))
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_trace_one_pass_blocks(q, orc, block):
+    """k_onepass + k_op_gather at a size past the fused limit, a ragged end,
+    every class reachable."""
+    n = (1 << 24) + 333
+    for kind, epss in (("b", (1e-15, 1e-8, 1e-1)), ("c", (1e-8,))):
+        x, y = workloads.pair(kind, n, 400 + block)
+        xd, yd = _dev(x), _dev(y)
+        for eps in epss:
+            _, units = check_trace(q, orc, x, y, eps, block, expect_kernel="k_onepass", xd=xd, yd=yd)
+            used = set(np.unique(units["source"]).tolist())
+            assert used <= {SRC["none"], SRC["slot0"], SRC["slot1"], SRC["slot3"], SRC["recomputed"]}
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_trace_one_pass_recomputed(q, orc, block):
+    """A ramp whose last component dwarfs the rest: the streaming kernel keeps
+    the wrong candidates for many blocks and the gather recomputes them; the
+    recomputed values must be those of the oracle, block by block."""
+    n = (1 << 24) + 77
+    rng = np.random.default_rng(17)
+    x = np.exp2(np.linspace(0.0, 40.0, n)) * rng.uniform(1.0, 2.0, n)
+    x[-1] = 2.0**60
+    y = rng.uniform(1.0, 2.0, n) * rng.choice([-1.0, 1.0], n)
+    x[rng.random(n) < 0.001] = 0.0  # blocks with zeros take the general route
+    _, units = check_trace(q, orc, x, y, 1e-8, block, path="one_pass")
+    assert np.count_nonzero(units["source"] == SRC["recomputed"]) > 0
+
+
+@pytest.mark.parametrize("eps", [1e-15, 1e-8, 1e-1])
+def test_trace_one_pass_components(q, orc, eps):
+    """k_onepass_items + k_op_gather_items (blocks of one component): the
+    per-component class map the kernels summed with, and every item's value;
+    lognormal, uniform with outliers, zeros (statistics-only items), and a
+    spike at the end (every item recomputed)."""
+    n = (1 << 24) + 77
+    rng = np.random.default_rng(23)
+    xb, yb = workloads.pair("b", n, 61)
+    xc, yc = workloads.pair("c", n, 62)
+    sparse = xb.copy()
+    sparse[rng.random(n) < 0.02] = 0.0
+    spike = xc.copy()
+    spike[-1] = 1e30
+    for x, y, need_rec in ((xb, yb, False), (xc, yc, False), (sparse, yb, True), (spike, yc, True)):
+        _, units = check_trace(q, orc, x, y, eps, 1, expect_kernel="k_onepass_items")
+        assert set(np.unique(units["source"]).tolist()) <= {SRC["item"], SRC["item_recomputed"]}
+        if need_rec:
+            assert np.count_nonzero(units["source"] == SRC["item_recomputed"]) > 0
+
+
+def test_trace_repeatable_bit_for_bit(q, orc):
+    """The one-pass path's speculation depends on timing (a shared running
+    bound of e_max), but every candidate has one definition: repeated calls
+    return the same bits, unit by unit, for blocks of 32 and 256 and for
+    single components."""
+    n = (1 << 25) + 333
+    x, y = workloads.pair("b", n, 2107)
+    xd, yd = _dev(x), _dev(y)
+    for block in (32, 256, 1):
+        first = None
+        for _ in range(4):
+            r, units, per, _ = q.trace(xd, yd, eps=1e-8, block=block, path="one_pass", want_cls=False)
+            key = (np.float64(r.value).tobytes(), units["value"].tobytes(), units["grid"].tobytes(),
+                   units["cls"].tobytes())
+            if first is None:
+                first = key
+            assert key == first
+        for _ in range(3):
+            r2 = q.qdot(xd, yd, eps=1e-8, block=block, path="one_pass")
+            assert np.float64(r2.value).tobytes() == first[0]
+
+
+def test_fused_and_one_pass_agree_bit_for_bit(q, orc):
+    """The fused and one-pass paths form every candidate the same way, so on
+    the same data they return the same bits (blocks of 32 .. 256)."""
+    n = (1 << 21) + 77
+    for kind in ("b", "c"):
+        x, y = workloads.pair(kind, n, 500)
+        xd, yd = _dev(x), _dev(y)
+        for block in (32, 64, 128, 256):
+            for eps in (1e-15, 1e-8, 1e-1):
+                ra, ua, _, _ = q.trace(xd, yd, eps=eps, block=block, path="fused")
+                rb, ub, _, _ = q.trace(xd, yd, eps=eps, block=block, path="one_pass")
+                assert np.float64(ra.value).tobytes() == np.float64(rb.value).tobytes()
+                assert ra.count == rb.count
+                assert np.array_equal(ua["cls"], ub["cls"])
+                kept = ua["cls"] != 0
+                assert np.array_equal(ua["value"][kept], ub["value"][kept])
+                assert np.array_equal(ua["grid"][kept], ub["grid"][kept])
+
+
+def test_trace_full_size_benched_cell(q, orc):
+    """The benchmark's own cell (n = 2^28, lognormal sigma = 4, blocks of 32,
+    eps = 1e-8, the same seed and launch shape as bench.py), unit by unit."""
+    n = 1 << 28
+    x, y = workloads.pair("b", n, 2106)
+    check_trace(q, orc, x, y, 1e-8, 32, expect_kernel="k_onepass")
+
+
+def test_trace_rejects_two_pass(q):
+    import torch
+    x = torch.ones(1000, dtype=torch.float64, device="cuda")
+    with pytest.raises(q.QdotError):
+        q.trace(x, x, eps=1e-8, block=0)
+    with pytest.raises(q.QdotError):
+        q.trace(x, x, eps=1e-8, block=8)

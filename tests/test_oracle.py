@@ -328,3 +328,126 @@ def test_backward_oracle(orc):
         fm = Fraction(g) * sum(Fraction(a) * Fraction(b) for a, b, k in zip(xm, qy, keep) if k)
         fd = float((fp - fm) / (Fraction(xp[i]) - Fraction(xm[i])))
         assert fd == pytest.approx(gx[i], rel=1e-12, abs=0)
+
+
+def _adversarial_pairs():
+    """Small vectors with mixed signs, subnormals, huge and tiny magnitudes and
+    exact cancellation: the cases a sloppy exact accumulator gets wrong."""
+    rng = np.random.default_rng(77)
+    cases = []
+    tiny = [5e-324, 3 * 2.0**-1074, 2.0**-1022, 1e-310, -7e-320]
+    huge = [1e150, -1e148, 2.0**490, -2.0**480, 3.0 * 2.0**450]  # products and sums stay finite
+    for t in range(12):
+        n = int(rng.integers(1, 65))
+        x = rng.choice(tiny + huge + [1.0, -1.0, 0.0, 1e-300, 2.0**-60], n) * rng.uniform(0.5, 2.0, n)
+        y = rng.choice(tiny + huge + [1.0, -3.0, 0.0, 1e-8], n) * rng.uniform(0.5, 2.0, n)
+        cases.append((x, y))
+    # exact cancellation: x.y = a - a + small
+    a = 2.0**500
+    cases.append((np.array([a, 1.0, -a, 2.0**-700]), np.array([a, 3.0, a, 1.0])))
+    # random signs over a wide exponent range
+    for t in range(6):
+        n = int(rng.integers(1, 65))
+        x = rng.choice([-1.0, 1.0], n) * np.exp2(rng.uniform(-1000, 500, n))
+        y = rng.choice([-1.0, 1.0], n) * np.exp2(rng.uniform(-1000, 500, n))
+        cases.append((x, y))
+    return cases
+
+
+def test_abs_dot_and_sum_exact_pinned(orc):
+    """orc.abs_dot_exact (the scale of every GPU parity tolerance) and
+    orc.sum_exact equal the correctly rounded exact rational results
+    (Fraction sums of the same doubles), on adversarial inputs."""
+    for x, y in _adversarial_pairs():
+        ax = sum((abs(Fraction(a) * Fraction(b)) for a, b in zip(x, y)), Fraction(0))
+        assert orc.abs_dot_exact(x, y) == float(ax)
+        sx = sum((Fraction(v) for v in x), Fraction(0))
+        assert orc.sum_exact(x) == float(sx)
+        d = sum((Fraction(a) * Fraction(b) for a, b in zip(x, y)), Fraction(0))
+        assert orc.dot_exact(x, y) == float(d)
+    # a sum whose exact value is a tie between two doubles rounds to even
+    v = np.array([1.0, 2.0**-53])
+    assert orc.sum_exact(v) == 1.0
+    v = np.array([1.0 + 2.0**-52, 2.0**-53])
+    assert orc.sum_exact(v) == 1.0 + 2.0**-51
+
+
+def test_value_ld_within_long_double_rounding(orc):
+    """value_ld (the long-double accumulation of the quantized products) is
+    within the rounding of a long-double sum of n products of the exact sum:
+    |value_ld - z_exact| <= (n + 2) eps_ld sum|q(x) q(y)| + 2^-53 |z_exact|,
+    eps_ld the long-double machine epsilon of this host (64-bit significand
+    on x86-64, 113-bit on AArch64)."""
+    eps_ld = Fraction(float(np.finfo(np.longdouble).eps))
+    for kind in ("a", "b", "c", "cfg0"):
+        for seed in range(3):
+            x, y = workloads.pair(kind, 300, 500 + seed)
+            for block in (0, 1, 32):
+                for eps in (1e-16, 1e-6, 1e-2):
+                    r = orc.qdot(x, y, eps=eps, block=block, explain=True)
+                    exact = _frac_sum(r.qx, r.qy, r.cls)
+                    sabs = sum((abs(Fraction(a) * Fraction(b)) for a, b, c in zip(r.qx, r.qy, r.cls)
+                                if c in (1, 2, 3)), Fraction(0))
+                    tol = (len(x) + 2) * eps_ld * sabs + Fraction(2) ** -53 * abs(exact)
+                    assert abs(Fraction(r.value_ld) - exact) <= tol
+
+
+@pytest.mark.parametrize("unit", [1, 7, 32, 256])
+@pytest.mark.parametrize("block", [0, 1, 32])
+def test_unit_sums_bruteforce(orc, unit, block):
+    """Algorithm 1's partial sums over index ranges: each range's sum of
+    q(x_i) q(y_i) and of |x_i y_i| equals the correctly rounded Fraction sum
+    over the same range (classes and q values from the pinned explain
+    output); together they add up to z."""
+    for kind in ("a", "b", "c"):
+        x, y = workloads.pair(kind, 300, 70 + unit + block)
+        x[::17] = 0.0
+        for eps in (1e-16, 1e-6, 0.5):
+            r = orc.qdot(x, y, eps=eps, block=block, explain=True)
+            sums, abss = orc.unit_sums(x, y, unit, eps=eps, block=block)
+            assert len(sums) == (len(x) + unit - 1) // unit
+            for k in range(len(sums)):
+                sl = slice(k * unit, (k + 1) * unit)
+                q = _frac_sum(r.qx[sl], r.qy[sl], r.cls[sl])
+                a = sum((abs(Fraction(p) * Fraction(t)) for p, t in zip(x[sl], y[sl])), Fraction(0))
+                assert sums[k] == float(q)
+                assert abss[k] == float(a)
+            tot = sum((Fraction(v) for v in sums), Fraction(0))
+            assert abs(tot - _frac_sum(r.qx, r.qy, r.cls)) <= len(sums) * Fraction(2) ** -53 * sum(
+                (abs(Fraction(v)) for v in sums), Fraction(0))
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_oracle_equals_serial(orc, threads):
+    """The CPU-baseline helper that spreads the oracle over host threads gives
+    exactly the serial oracle's value, counts and statistics (exact sums are
+    order independent), zeros, subnormals and non-finite values included."""
+    rng = np.random.default_rng(threads)
+    for kind in ("a", "b", "c", "cfg0"):
+        x, y = workloads.pair(kind, 20011, 40 + threads)
+        x[rng.random(x.shape[0]) < 0.01] = 0.0
+        y[::997] = 5e-324
+        for block in (0, 1, 7, 32, 256):
+            for eps in (1e-16, 1e-8, 1e-2):
+                a = orc.qdot(x, y, eps=eps, block=block)
+                b = orc.qdot_threads(x, y, eps=eps, block=block, threads=threads)
+                assert b.status == 0
+                assert np.float64(a.value).tobytes() == np.float64(b.value).tobytes()
+                assert a.count == b.count
+                assert (a.e_max, a.e_min, a.n_bins, a.f) == (b.e_max, b.e_min, b.n_bins, b.f)
+    x = np.ones(100)
+    x[50] = np.nan
+    assert orc.qdot_threads(x, np.ones(100), eps=1e-8, threads=threads).status == 2
+
+
+def test_cpu_fp64_dot_within_rounding(orc):
+    """The host FP64 dot (one fused multiply-add chain per thread, partials
+    added in order) is within the rounding bound of such a sum of the exact
+    dot: |dot - x.y| <= (n / t + t + 1) 2^-53 sum |x_i y_i|."""
+    for kind in ("a", "b", "c"):
+        x, y = workloads.pair(kind, 100003, 9)
+        ex = Fraction(orc.dot_exact(x, y))
+        sabs = Fraction(orc.abs_dot_exact(x, y))
+        for t in (1, 4, 8):
+            d = orc.dot_fp64(x, y, t)
+            assert abs(Fraction(d) - ex) <= Fraction(x.shape[0] // t + t + 2, 2**53) * sabs

@@ -54,6 +54,24 @@ def test_static_scratch_matches_qdot_twice_in_a_row(env, orc):
             assert abs(r.value - ref.value) <= tol
 
 
+def test_static_scratch_eight_byte_aligned_inputs(env, orc):
+    """Inputs that are only 8-byte aligned take the 64-bit load variant; blocks
+    of 64 then keep per-block keys in the scratch (2 bytes per block), which
+    still fits at this size."""
+    torch, q, lib = env
+    x, y = workloads.pair("b", 200001, 77)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    xs, ys = xd[1:], yd[1:]
+    assert xs.data_ptr() % 16 == 8
+    tol = TOL * orc.abs_dot_exact(x[1:], y[1:])
+    for block in (32, 64, 0):
+        ref = q.qdot(xs, ys, eps=1e-8, block=block)
+        for _ in range(2):
+            r = _static_call(torch, q, lib, xs, ys, 1e-8, block)
+            assert r.count == ref.count and r.n_bins == ref.n_bins
+            assert abs(r.value - ref.value) <= tol
+
+
 def test_static_scratch_rejects_arguments_that_do_not_fit(env):
     torch, q, lib = env
     x = torch.ones(16, dtype=torch.float64, device="cuda")

@@ -18,6 +18,14 @@ benchmark configuration describe):
 * ``poisson3d`` / ``poisson2d``: SPD variable-coefficient 7-point / 5-point
   operators, coefficient 10**U(-3, 3) per cell, harmonic-mean face
   coefficients, Dirichlet boundary faces adding c_i to the diagonal.
+* ``stencil27``: the SPD 27-point operator of the paper's ACG problems (Sec.
+  4.2, the HPCCG "chimney" boxes nx x ny x nz): 27 on the diagonal, -1 for
+  every grid neighbour within one step along each axis, with
+  ``ones_rhs`` = A times the all-ones vector (so x = 1 solves it).
+* ``graph_laplacian``: L = D - W of a seeded random undirected graph (every
+  vertex draws ``degree`` partners uniformly, unit weights, the edge set
+  symmetrised), the stand-in for the paper's random graph Laplacians of
+  Sec. 4.3.
 """
 from __future__ import annotations
 
@@ -193,7 +201,7 @@ def batched_cg_systems(count: int = 256, lo: int = 16, hi: int = 64, seed: int =
 
 
 def exponent_dist(kind: str, n: int, t: float, seed: int, device="cuda"):
-    """The paper's synthetic arrays (Sec. 6.1): components s * 2^p with
+    """The paper's synthetic arrays (Sec. 4.1): components s * 2^p with
     s ~ U[0.5, 1) and p ~ U[-t/2, t/2] (kind 'A') or p ~ N(0, t/2) (kind 'B'),
     drawn on `device` from a seeded torch generator; float64."""
     import torch
@@ -206,3 +214,62 @@ def exponent_dist(kind: str, n: int, t: float, seed: int, device="cuda"):
     else:
         raise ValueError(kind)
     return s * torch.exp2(p)
+
+
+def stencil27(nx: int, ny: int, nz: int):
+    """27-point operator on an nx x ny x nz box (lexicographic order, x
+    fastest): row i has 27 on the diagonal and -1 for each grid point within
+    one step of it along every axis; CSR (rowptr int64, col int32, val f64),
+    columns ascending.  Strictly diagonally dominant, so SPD.  Built one z
+    plane at a time so the 10^7-row boxes stay within a few GB."""
+    n = nx * ny * nz
+    offs = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]  # ascending columns
+    ix = np.tile(np.arange(nx, dtype=np.int64), ny)
+    iy = np.repeat(np.arange(ny, dtype=np.int64), nx)
+    plane = nx * ny
+    cols, vals, counts = [], [], []
+    for z in range(nz):
+        base = z * plane + iy * nx + ix
+        cm, vm, km = [], [], []
+        for dz, dy, dx in offs:
+            ok = (0 <= ix + dx) & (ix + dx < nx) & (0 <= iy + dy) & (iy + dy < ny) & (0 <= z + dz) & (z + dz < nz)
+            cm.append(np.where(ok, base + dx + nx * dy + plane * dz, -1))
+            km.append(ok)
+            vm.append(27.0 if (dz, dy, dx) == (0, 0, 0) else -1.0)
+        C = np.stack(cm, axis=1)
+        K = np.stack(km, axis=1)
+        V = np.broadcast_to(np.array(vm), C.shape)
+        cols.append(C[K].astype(np.int32))
+        vals.append(V[K].astype(np.float64))
+        counts.append(K.sum(axis=1))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.concatenate(counts), out=rowptr[1:])
+    return rowptr, np.concatenate(cols), np.concatenate(vals)
+
+
+def ones_rhs(rowptr, col, val) -> np.ndarray:
+    """b = A 1 (row sums, summed exactly as integers for the 27-point
+    operator's integer entries)."""
+    sums = np.add.reduceat(val, rowptr[:-1]) if val.size else np.zeros(rowptr.shape[0] - 1)
+    sums[rowptr[1:] == rowptr[:-1]] = 0.0
+    return sums
+
+
+def graph_laplacian(n: int, degree: int = 8, seed: int = 2113):
+    """L = D - W of a random undirected graph on n vertices: each vertex draws
+    `degree` partners uniformly (self loops dropped), every drawn edge is
+    made symmetric, weights are 1 (repeated draws count once).  CSR (rowptr
+    int64, col int32, val f64), columns ascending.  Symmetric, positive
+    semi-definite, rows sum to 0."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    src = np.repeat(np.arange(n, dtype=np.int64), degree)
+    dst = rng.integers(0, n, src.shape[0])
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    W = sp.coo_matrix((np.ones(src.shape[0]), (src, dst)), shape=(n, n)).tocsr()
+    W = ((W + W.T) > 0).astype(np.float64)
+    deg = np.asarray(W.sum(axis=1)).ravel()
+    L = (sp.diags(deg) - W).tocsr()
+    L.sort_indices()
+    return L.indptr.astype(np.int64), L.indices.astype(np.int32), L.data.astype(np.float64)
