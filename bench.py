@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "cg", "cg_batched", "power", "backward", "paper"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "cg", "cg_batched", "power", "backward", "paper",
+                                                       "paper_solvers"])
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-1e-10 summary of the single line")
     ap.add_argument("--grid", type=int, default=128, help="CG grid edge (cg workload)")
     ap.add_argument("--cg-coef", default="variable", choices=["variable", "const"],
@@ -412,20 +413,53 @@ def timed_cg(A, bd, eps, block, dot, reps=1, max_it=200000):
 
 
 def cg_summary(args, edge=128):
-    """ACG on the variable-coefficient 7-point Poisson problem (edge^3 grid):
-    time to relative residual 1e-10 with qdot dots against FP64 dots."""
-    A, bd, nnz = cg_problem(edge)
+    """ACG (Algorithm 4) to relative residual 1e-10 with qdot dot products,
+    against the same solver with plain FP64 dots, in the paper's protocol
+    (Sec. 4.2, "qdot with Conjugate Gradient"):
+    - the constant-coefficient 7-point operator on edge^3 (well-conditioned,
+      like the paper's HPCCG problems): eps swept x10 from 1e-16 to 1e3 with
+      blocks of 32; the largest eps whose iteration count equals the FP64-dot
+      count, with its time to solution and class counts;
+    - the variable-coefficient operator (coefficients 10^U(-3,3)) at eps
+      1e-8 (every component DOUBLE) and at eps values that lower components.
+    Times are CUDA-event seconds per solve, best of 2 after a warm-up solve."""
+    out = {"protocol": "x0 = 0, stop at ||r||/||b|| <= 1e-10; eps x10 from 1e-16 to 1e3; blocks of 32"}
+    A, bd, nnz = cg_problem(edge, "const")
+    timed_cg(A, bd, 1e-16, 0, "fp64")
+    t64, i64 = timed_cg(A, bd, 1e-16, 0, "fp64", reps=2)
+    sweep, best = [], None
+    for k in range(-16, 4):
+        eps = 10.0 ** k
+        t, inf = timed_cg(A, bd, eps, 32, "qdot", reps=2, max_it=20 * i64["iters"])
+        row = {"eps": eps, "iters": inf["iters"], "seconds": t, "status": inf["status"],
+               "true_relres": inf["true_relres"], "class_counts": list(inf["counts"])}
+        sweep.append(row)
+        if inf["status"] == 0 and inf["iters"] == i64["iters"]:
+            best = row
+    out["const_coef"] = {
+        "problem": f"7-point constant-coefficient Poisson {edge}^3 (n={A.n}, nnz={nnz}), rhs U(-1,1)",
+        "fp64_dot": {"seconds": t64, "iters": i64["iters"], "true_relres": i64["true_relres"]},
+        "largest_eps_equal_iters": best["eps"] if best else None,
+        "at_largest_eps": best,
+        "time_ratio_qdot_over_fp64": best["seconds"] / t64 if best else None,
+        "sweep": sweep}
+    A, bd, nnz = cg_problem(edge, "variable")
     timed_cg(A, bd, args.eps, args.block, "qdot")  # warm-up (graph instantiation, clocks)
-    t_q, iq = timed_cg(A, bd, args.eps, args.block, "qdot")
     t_d, idd = timed_cg(A, bd, 1e-16, 0, "fp64")
-    return {"problem": f"7-point variable-coefficient Poisson {edge}^3 (n={A.n}, nnz={nnz}), coefficients "
-                       f"10^U(-3,3), rhs U(-1,1), x0 = 0, stop at ||r||/||b|| <= 1e-10",
-            "qdot": {"eps": args.eps, "block": args.block, "seconds": t_q, "iters": iq["iters"],
-                     "status": iq["status"], "true_relres": iq["true_relres"], "class_counts": list(iq["counts"])},
-            "fp64_dot": {"seconds": t_d, "iters": idd["iters"], "status": idd["status"],
-                         "true_relres": idd["true_relres"]},
-            "iters_equal": iq["iters"] == idd["iters"],
-            "time_ratio_qdot_over_fp64": t_q / t_d}
+    runs = []
+    for eps in (args.eps, 1e-4, 1e-2):
+        t_q, iq = timed_cg(A, bd, eps, args.block, "qdot")
+        runs.append({"eps": eps, "block": args.block, "seconds": t_q, "iters": iq["iters"], "status": iq["status"],
+                     "true_relres": iq["true_relres"], "class_counts": list(iq["counts"]),
+                     "iters_rel_diff": (iq["iters"] - idd["iters"]) / idd["iters"],
+                     "time_ratio_qdot_over_fp64": t_q / t_d})
+    out["variable_coef"] = {
+        "problem": f"7-point variable-coefficient Poisson {edge}^3 (n={A.n}, nnz={nnz}), coefficients "
+                   f"10^U(-3,3), rhs U(-1,1)",
+        "fp64_dot": {"seconds": t_d, "iters": idd["iters"], "status": idd["status"],
+                     "true_relres": idd["true_relres"]},
+        "runs": runs}
+    return out
 
 
 def run_cg(args, rank, world, local, dist, lib):
@@ -643,6 +677,85 @@ def run_paper(args, rank, world, local, dist, lib):
     }
 
 
+def run_paper_solvers(args, rank, world, local, dist, lib):
+    """The paper's ACG and APM protocols (Sec. 4.2, 4.3) on its problem shapes.
+    ACG: the 27-point operator on the chimney boxes 100x100x1, 1000x1000x1,
+    100x100x10 and 1000x1000x10, b = A 1, x0 = 0, stopped on ||r|| <= tau =
+    1e-8; qdot with exact binning (Algorithm 2), eps x10 from 1e-16 to 1e3;
+    the largest eps whose iteration count equals the FP64-dot CG's.  APM:
+    random graph Laplacians with n = 1e4 and 1e5, tau = 1e-6, at most 300
+    iterations; the largest eps whose eigenvalue is within tau of the FP64-dot
+    power method's.  The paper's own largest eps values are printed beside
+    ours (its HPCCG and Laplacian generators are replaced by seeded ones)."""
+    import numpy as np
+    import torch
+
+    import paper_2105_00115_gb300 as q
+    import workloads
+    t_start = time.perf_counter()
+    cg_rows = []
+    paper_cg = {(100, 100, 1): 1e0, (1000, 1000, 1): 1e3, (100, 100, 10): 1e2, (1000, 1000, 10): 1e2}
+    for shape, paper_eps in paper_cg.items():
+        rp, col, val = workloads.stencil27(*shape)
+        b = workloads.ones_rhs(rp, col, val)
+        rel = 1e-8 / float(np.linalg.norm(b))
+        A = q.Csr(rp, col, val)
+        bd = torch.from_numpy(b).cuda()
+        del rp, col, val
+        q.cg(A, bd, rel_tol=rel, max_it=100000, dot="fp64")  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, i64, _ = q.cg(A, bd, rel_tol=rel, max_it=100000, dot="fp64")
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) * 1e-3
+        sweep, best = [], None
+        for k in range(-16, 4):
+            eps = 10.0 ** k
+            e0.record()
+            _, inf, _ = q.cg(A, bd, rel_tol=rel, max_it=20 * i64["iters"] + 100, eps=eps, block=0)
+            e1.record()
+            torch.cuda.synchronize()
+            row = {"eps": eps, "iters": inf["iters"], "seconds": e0.elapsed_time(e1) * 1e-3,
+                   "status": inf["status"], "true_relres": inf["true_relres"], "class_counts": list(inf["counts"])}
+            sweep.append(row)
+            if inf["status"] == 0 and inf["iters"] == i64["iters"]:
+                best = eps
+        cg_rows.append({"problem": f"27-point {shape[0]}x{shape[1]}x{shape[2]} (n={A.n})",
+                        "fp64_dot": {"iters": i64["iters"], "seconds": t64, "true_relres": i64["true_relres"]},
+                        "largest_eps_equal_iters": best, "paper_largest_eps": paper_eps, "sweep": sweep})
+        del A, bd
+        torch.cuda.empty_cache()
+    pm_rows = []
+    for n in (10000, 100000):
+        rp, col, val = workloads.graph_laplacian(n, 8)
+        A = q.Csr(rp, col, val)
+        x0 = torch.from_numpy(workloads.unit_start(n)).cuda()
+        lam64, _, i64, _ = q.power(A, x0, iters=300, tau=1e-6, dot="fp64")
+        sweep, best = [], None
+        for k in range(-16, 4):
+            eps = 10.0 ** k
+            lam, _, inf, _ = q.power(A, x0, iters=300, tau=1e-6, eps=eps, block=0)
+            err = abs(lam - lam64)
+            sweep.append({"eps": eps, "iters": inf["iters"], "lambda": lam, "abs_err_vs_fp64_pm": err,
+                          "status": inf["status"], "class_counts": list(inf["counts"])})
+            if inf["status"] == 0 and err <= 1e-6:
+                best = eps
+        pm_rows.append({"problem": f"random graph Laplacian n={n}, degree 8", "fp64_dot": {"iters": i64["iters"],
+                        "lambda": lam64}, "largest_eps_within_tau": best, "paper_largest_eps": 1e-7,
+                        "sweep": sweep})
+    total = time.perf_counter() - t_start
+    return {
+        "metric": "ACG / APM paper protocol (largest qdot eps keeping FP64 convergence)", "value": total,
+        "unit": "s (whole protocol)", "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * total,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "paper ACG (27-point chimney boxes, tau 1e-8) and APM (graph Laplacians, "
+                               "tau 1e-6, 300 iterations), exact binning, eps 1e-16 .. 1e3"},
+        "acg": cg_rows, "apm": pm_rows, "cpu_baseline": None, "e2e": None,
+    }
+
+
 def run_power(args, rank, world, local, dist, lib):
     """Power-method workload: 500 APM iterations on the 2048^2 5-point operator."""
     import torch
@@ -798,7 +911,8 @@ def main():
     lib = q.load()
     if args.workload != "single":
         fn = {"batched": run_batched, "cg": run_cg, "cg_batched": run_cg_batched, "power": run_power,
-              "backward": run_backward, "paper": run_paper}[args.workload]
+              "backward": run_backward, "paper": run_paper,
+                "paper_solvers": run_paper_solvers}[args.workload]
         line = fn(args, rank, world, local, dist, lib)
         if rank == 0:
             print(json.dumps(line), flush=True)

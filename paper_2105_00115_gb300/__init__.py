@@ -170,7 +170,7 @@ def trace(x, y, eps=1e-16, block=32, split_budget=1, mant_reading=0, path="auto"
     out = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=x.device)
     units = torch.zeros(max(nunits, 1) * ctypes.sizeof(TraceUnit), dtype=torch.uint8, device=x.device)
     cls = None
-    if want_cls and lib.qdot_stream_kernel(n, ctypes.byref(p), al16) == b"k_onepass_items":  # item records
+    if want_cls and per.value == 256 and block != 256:  # item units: per-component classes too
         cls = torch.full((n,), 255, dtype=torch.uint8, device=x.device)
     st = lib.qdot_trace(_ptr(x), _ptr(y), n, ctypes.byref(p), _ptr(out), _ptr(units), nunits, _ptr(cls), _ptr(ws),
                         ws.numel(), _stream_ptr(stream))

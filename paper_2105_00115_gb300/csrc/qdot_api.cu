@@ -107,7 +107,7 @@ PathChoice choose_path(int64_t n, const qdot_params* p, bool al16) {
 size_t workspace_for(int64_t n, const qdot_params* p, bool al16, PathChoice* choice) {
   PathChoice c = choose_path(n, p, al16);
   if (choice) *choice = c;
-  if (c == kFused) return fused_ws_bytes();
+  if (c == kFused) return fused_ws_bytes(p);
   if (c == kOnePass) return plan_one_pass(n, p).total;
   return plan_two_pass(n, p, al16).total;
 }
@@ -260,7 +260,9 @@ int64_t qdot_trace_units(int64_t n, const qdot_params* p, int32_t al16, int32_t*
   if (!valid_params(n, p, &why)) return 0;
   const PathChoice c = choose_path(n, p, al16 != 0);
   if (c == kTwoPass) return 0;
-  const bool items = c == kOnePass && plan_one_pass(n, p).items;
+  // item units: the one-pass item records, and the fused kernel for exact
+  // binning and blocks of one
+  const bool items = (c == kOnePass && plan_one_pass(n, p).items) || (c == kFused && p->block <= 1);
   const int64_t per = items ? 256 : p->block;
   if (unit_components) *unit_components = (int32_t)per;
   return (n + per - 1) / per;
@@ -402,7 +404,7 @@ const char* qdot_stream_kernel(int64_t n, const qdot_params* p, int32_t al16) {
   std::string why;
   if (!valid_params(n, p, &why)) return "";
   const PathChoice c = choose_path(n, p, al16 != 0);
-  if (c == kFused) return "k_qdot_fused";
+  if (c == kFused) return fused_stream_kernel(p);
   if (c == kOnePass) return one_pass_stream_kernel(n, p);
   return "k_apply_fast";
 }

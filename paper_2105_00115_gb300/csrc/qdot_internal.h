@@ -81,7 +81,8 @@ cudaError_t launch_one_pass(const double* x, const double* y, int64_t n, const q
 // One-launch qdot for vectors the resident grid covers in a few items
 // (cooperative launch with grid-wide barriers).
 bool fused_supported(int64_t n, const qdot_params* p, bool aligned16);
-size_t fused_ws_bytes();
+size_t fused_ws_bytes(const qdot_params* p);
+const char* fused_stream_kernel(const qdot_params* p);
 cudaError_t launch_fused(const double* x, const double* y, int64_t n, const qdot_params* p, void* ws,
                          qdot_result* out, qdot_selection* sel, cudaStream_t stream, TraceOut trace = TraceOut());
 

@@ -99,10 +99,10 @@ constexpr int kExchange = 2;
 // fewer blocks per item their gather is already short, and the items every
 // warp recomputes (its first two) would cost more than they save.
 constexpr long long kItemPathMinN = 1ll << 25;
-// Off: the item records for blocks of 32 are built and measured faster, but
-// a fix to them (every lane now joins the block shuffles of the statistics
-// branch) has not yet run on a GPU.
-constexpr bool kItemPathForBlocks = false;
+// Blocks of 32 take the item records from kItemPathMinN on: one 16-byte
+// record per 256 components instead of 12 to 20 bytes per block, and a
+// gather that reads 16 times less.
+constexpr bool kItemPathForBlocks = true;
 
 // Blocks a gather CTA can queue for recomputation by its warps together.
 constexpr int kRepairQueue = 512;
@@ -553,49 +553,6 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
 // non-finite values or the vectors' end inside it).
 constexpr unsigned long long kItemRecompute = 1ull << 63;
 
-// Quantized products of a lane's 8 components into aF (FP64, relative to
-// 2^u), each with its own class cls[j] (kPerf .. kDouble).  RMODE
-// (warp-uniform): bit 0 some component is SINGLE, bit 1 some is HALF, bit 2
-// some is perforated.
-template <int RMODE>
-__device__ __forceinline__ void acc_components(const Chunk& ch, const int (&key)[8], int u, const int (&cls)[8],
-                                               double& aF) {
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t hx = (uint32_t)(ch.x[j] >> 32), lx = (uint32_t)ch.x[j];
-    const uint32_t hy = (uint32_t)(ch.y[j] >> 32), ly = (uint32_t)ch.y[j];
-    const int d = u - key[j];
-    const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
-    uint64_t xo = ((uint64_t)((hx & 0x800FFFFFu) | 0x3FF00000u) << 32) | lx;
-    uint64_t yo = ((uint64_t)((hy & 0x800FFFFFu) | ye) << 32) | ly;
-    if (RMODE & 1) {  // SINGLE components: round to nearest even at bit 29
-      const bool rs = cls[j] == kSingle;
-      const uint32_t inc = rs ? 0x0FFFFFFFu : 0u, bit = rs ? 1u : 0u, mask = rs ? 0xE0000000u : ~0u;
-      xo = (xo + (inc + (((uint32_t)xo >> 29) & bit))) & (0xFFFFFFFF00000000ull | mask);
-      yo = (yo + (inc + (((uint32_t)yo >> 29) & bit))) & (0xFFFFFFFF00000000ull | mask);
-    }
-    if ((RMODE & 2) && cls[j] == kHalf) {
-      xo = round_bits<42>(xo);
-      yo = round_bits<42>(yo);
-    }
-    if ((RMODE & 4) && cls[j] == kPerf) xo = 0ull;
-    aF = fma(__longlong_as_double((long long)xo), __longlong_as_double((long long)yo), aF);
-  }
-}
-
-__device__ __forceinline__ void acc_components_mode(unsigned rmode, const Chunk& ch, const int (&key)[8], int u,
-                                                    const int (&cls)[8], double& aF) {
-  switch (rmode) {  // warp-uniform
-    case 0: acc_components<0>(ch, key, u, cls, aF); break;
-    case 1: acc_components<1>(ch, key, u, cls, aF); break;
-    case 2: acc_components<2>(ch, key, u, cls, aF); break;
-    case 3: acc_components<3>(ch, key, u, cls, aF); break;
-    case 4: acc_components<4>(ch, key, u, cls, aF); break;
-    case 5: acc_components<5>(ch, key, u, cls, aF); break;
-    case 6: acc_components<6>(ch, key, u, cls, aF); break;
-    default: acc_components<7>(ch, key, u, cls, aF); break;
-  }
-}
 
 // Streaming kernel with item records.  LOG2B = 0: blocks of one component,
 // each quantized to the class of its score key - e_lo - f_spec + 1.  LOG2B =
@@ -743,118 +700,6 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
   }
 }
 
-// One item recomputed by a warp with the final classes, on the streaming
-// layout and the chains of the streaming kernel (any components: zeros,
-// subnormals, the vectors' end).  Returns the item's sum on the grid
-// 2^(u - 52) (u its largest key, unbiased, in *u_out; kNone if the item has no
-// nonzero component), adds the lane's class counts to c and, when tcls is
-// given (qdot_trace), writes each component's class.
-template <int LOG2B>
-__device__ long long recompute_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
-                                    long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
-                                    unsigned long long (&c)[5], uint8_t* __restrict__ tcls) {
-  constexpr int LB = LOG2B ? LOG2B : 8;  // the item layout (blocks of one: that of 256)
-  constexpr int L = Map<LB>::L;
-  Chunk ch;
-  load_item<LB>(x, y, n, item, lane, ch);
-  int key[8];
-  bool nz[8];
-  int cmax = kNone, m = 0;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint64_t a = ch.x[j], b = ch.y[j];
-    nz[j] = ((ch.vmask >> j) & 1u) && !(is_zero(a) || is_zero(b) || is_nonfinite(a) || is_nonfinite(b));
-    key[j] = nz[j] ? exponent_of(a) + exponent_of(b) + 2046 : kNone;  // biased
-    cmax = max(cmax, key[j]);
-    m += nz[j];
-  }
-  const int u = __reduce_max_sync(0xffffffffu, cmax);
-  int cls[8];
-  if (LOG2B == 0) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) cls[j] = nz[j] ? (int)lut[key[j] - 2046 - kKeyMin] : kZero;
-  } else {  // the block key s_b = ceil(log2 M_b) + u_b over the block's L lanes
-    const int ub = group_max<L>(cmax), mb = group_sum_i<L>(m);
-    const int cb = mb ? (int)lut[ceil_log2_u32((uint32_t)mb) + ub - 2046 - kKeyMin] : kPerf;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) cls[j] = nz[j] ? cb : kZero;
-  }
-  if (tcls) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if ((ch.vmask >> j) & 1u) tcls[item * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls[j];
-  }
-  *u_out = u == kNone ? kNone : u - 2046;
-  if (u == kNone) return 0;  // warp-uniform
-  double a = 0.0;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    if (!nz[j]) continue;
-    c[cls[j]] += 1;
-    if (cls[j] == kPerf) continue;
-    uint64_t xo, yo;
-    chain_operands(ch.x[j], ch.y[j], u - key[j], xo, yo);
-    a = chain_step(xo, yo, cls[j], a);
-  }
-  long long v = __double2ll_rz(a * 4503599627370496.0);  // grid 2^(u - 52)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// recompute_item() on the streaming kernel's arithmetic, for an item whose
-// components are all in range, nonzero, normal and finite: the lanes load it
-// in the streaming layout and quantize with the final classes from the table
-// (per component, or per block from the block key log2 B + u_b).  Any other
-// item goes to recompute_item().
-template <int LOG2B>
-__device__ long long recompute_item_fast(const double* __restrict__ x, const double* __restrict__ y, long long n,
-                                         long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
-                                         unsigned long long (&c)[5], uint8_t* __restrict__ tcls) {
-  constexpr int LB = LOG2B ? LOG2B : 8;
-  constexpr int L = Map<LB>::L;
-  Chunk ch;
-  load_item<LB>(x, y, n, item, lane, ch);
-  int key[8];
-  int cmax = kNone, kmin = INT_MAX;
-  if (!__all_sync(0xffffffffu, chunk_keys(ch, key, cmax, kmin)))
-    return recompute_item<LOG2B>(x, y, n, item, lut, lane, u_out, c, tcls);
-  const int u = __reduce_max_sync(0xffffffffu, cmax);  // biased
-  *u_out = u - 2046;
-  double aF = 0.0;
-  if (LOG2B == 0) {
-    int cls[8];
-    unsigned seen = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      cls[j] = lut[key[j] - 2046 - kKeyMin];
-      seen |= 1u << cls[j];
-      c[cls[j]] += 1;
-    }
-    seen = __reduce_or_sync(0xffffffffu, seen);
-    acc_components_mode(((seen >> kSingle) & 1u) | (((seen >> kHalf) & 1u) << 1) | ((seen & 1u) << 2), ch, key, u,
-                        cls, aF);
-    if (tcls) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) tcls[item * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls[j];
-    }
-  } else {
-    const int cls = lut[LB + group_max<L>(cmax) - 2046 - kKeyMin];  // the block key s_b = log2 B + u_b
-    c[cls] += 8;
-    const unsigned prim = cls == kPerf ? 0u : 1u << cls;
-    double aH2 = 0.0, aS2 = 0.0;
-    acc_lane_mask<LB>(__reduce_or_sync(0xffffffffu, prim), 0u, ch, key, u, prim, aH2, aS2, aF);
-    if (!prim) aF = 0.0;
-    if (tcls) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) tcls[item * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls;
-    }
-  }
-  long long v = __double2ll_rz(aF * 4503599627370496.0);  // grid 2^(u - 52)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // Gather of item records: an item whose bound e_lo was e_max, and f_spec f, adds
 // its record; any other item is recomputed with the final classes.  The CTA

@@ -307,6 +307,62 @@ def test_fused_path(q, orc, block):
     assert lib.qdot_select_path(big, ctypes.byref(p), 1) == 2
 
 
+@pytest.mark.parametrize("block", [0, 1])
+def test_fused_bins_path(q, orc, block):
+    """Exact binning and blocks of one in one cooperative launch: statistics
+    (and the bin counts M_k) from one read, the sums from a second read out of
+    L2.  Every distribution, the 65536-component configuration of +-10^U(-8,0)
+    values, the solvers' sizes and the largest n the grid covers; past it the
+    call takes two passes."""
+    import ctypes
+    lib = q.load()
+    p = q.params(1e-8, block, 1, 0, "auto")
+    for n in (257, 65536, 1 << 20, 2097152 + 3, 3 * 10**6 + 1):
+        assert lib.qdot_select_path(n, ctypes.byref(p), 1) == 4  # QDOT_PATH_FUSED
+        assert lib.qdot_kernel_launches(n, ctypes.byref(p), 1) == 1
+        assert lib.qdot_stream_kernel(n, ctypes.byref(p), 1) == b"k_qdot_fused_bins"
+        for kind in ("a", "b", "c", "cfg0"):
+            if n > 65536 and kind in ("a", "cfg0"):
+                continue
+            x, y = workloads.pair(kind, n, 70 + block + n % 97)
+            for eps in (1e-16, 1e-8, 1e-3, 0.5):
+                _check(q, orc, x, y, eps, block, explain=False)
+    assert lib.qdot_select_path(1 << 23, ctypes.byref(p), 1) == 1  # two passes
+
+
+def test_fused_bins_edge_cases(q, orc):
+    """Zeros, subnormal products, a single component, all components equal
+    (one bin of M = n), and a bin count that is an exact power of two."""
+    rng = np.random.default_rng(5)
+    n = 100000
+    x, y = workloads.pair("b", n, 71)
+    z = x.copy()
+    z[rng.random(n) < 0.05] = 0.0
+    sub = x.copy()
+    sub[:1000] = 1e-310 * rng.uniform(1.0, 2.0, 1000)
+    ones = np.full(4096, 1.0 + 2.0**-20)
+    pow2 = np.concatenate([np.full(1024, 3.0), np.full(3000, 2.0**-30)])
+    cases = [(z, y), (sub, y), (x[:1], y[:1]), (ones, ones), (pow2, pow2[::-1].copy())]
+    for xx, yy in cases:
+        for block in (0, 1):
+            for eps in (1e-16, 1e-8, 2.0**-8, 4.0, 0.5):
+                _check(q, orc, xx, yy, eps, block, explain=False)
+
+
+def test_fused_bins_matches_item_path_bits(q, orc):
+    """Blocks of one: the fused launch and the one-pass item path quantize and
+    sum every item the same way, so they return the same bits."""
+    n = (1 << 21) + 77
+    for kind in ("b", "c"):
+        x, y = workloads.pair(kind, n, 72)
+        xd, yd = _dev(x), _dev(y)
+        for eps in (1e-15, 1e-8, 1e-1):
+            ra = q.qdot(xd, yd, eps=eps, block=1, path="fused")
+            rb = q.qdot(xd, yd, eps=eps, block=1, path="one_pass")
+            assert np.float64(ra.value).tobytes() == np.float64(rb.value).tobytes()
+            assert ra.count == rb.count
+
+
 def test_deterministic_repeat(q, orc):
     x, y = workloads.pair("c", 1 << 20, 5)
     xd, yd = _dev(x), _dev(y)

@@ -192,3 +192,73 @@ def test_cg_batched_iteration_cap_and_bad_column(q):
     col2[3] = int(off[1]) + 2
     x, infos = q.cg_batched(q.Csr(rp, col2, val), off, _dev(b), rel_tol=1e-10, max_it=50, eps=1e-16, block=32)
     assert all(i["status"] == q.QDOT_ERR_ARG for i in infos)
+
+
+# ---------------------------------------------------------------------------
+# The paper's problem shapes (Sec. 4.2 and 4.3): the 27-point operator on a
+# chimney-like box with b = A 1 and x0 = 0, stopped on an absolute residual
+# tau = 1e-8; the power method on a random graph Laplacian with tau = 1e-6 and
+# at most 300 iterations.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("block,eps", [(0, 1e-16), (0, 1.0), (0, 1e2), (32, 1e-8), (32, 1e2), (1, 1e-3)])
+def test_cg_stencil27_matches_oracle(q, orc, block, eps):
+    """27-point chimney-like box (30 x 30 x 3): the first iteration's class
+    counts equal the oracle's (identical inputs), and the whole solve takes the
+    oracle's iteration count (well-conditioned operator), to the same x."""
+    rp, col, val = workloads.stencil27(30, 30, 3)
+    n = rp.shape[0] - 1
+    b = workloads.ones_rhs(rp, col, val)
+    rel = 1e-8 / np.linalg.norm(b)  # Algorithm 4 stops on ||r|| <= tau = 1e-8
+    A = q.Csr(rp, col, val)
+    x, info, hist = q.cg(A, _dev(b), rel_tol=rel, max_it=2000, eps=eps, block=block, history=True)
+    xo, it, rr, counts, st = orc.cg(rp, col, val, b, rel_tol=rel, max_it=2000, eps=eps, block=block)
+    ref = orc.qdot(b, orc.spmv(rp, col, val, b), eps=eps, block=block)
+    np.testing.assert_array_equal(hist[0, 0], ref.count)
+    assert st == 0 and info["status"] == 0
+    assert info["iters"] == it
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    assert np.linalg.norm(xg - 1.0) <= 1e-6 * np.sqrt(n)
+
+
+def test_cg_stencil27_paper_protocol(q, orc):
+    """The paper's ACG protocol on a small chimney box: eps swept x10 from
+    1e-16 to 1e3 with exact binning; at every eps the GPU solver takes the
+    oracle's iteration count, and the largest eps that keeps the FP64-dot
+    count is the same on both sides."""
+    rp, col, val = workloads.stencil27(40, 40, 1)
+    b = workloads.ones_rhs(rp, col, val)
+    rel = 1e-8 / np.linalg.norm(b)
+    A = q.Csr(rp, col, val)
+    bd = _dev(b)
+    _, i64, _ = q.cg(A, bd, rel_tol=rel, max_it=5000, dot="fp64")
+    best_gpu = best_orc = None
+    for k in range(-16, 4):
+        eps = 10.0 ** k
+        _, info, _ = q.cg(A, bd, rel_tol=rel, max_it=5000, eps=eps, block=0)
+        _, it, _, _, st = orc.cg(rp, col, val, b, rel_tol=rel, max_it=5000, eps=eps, block=0)
+        assert info["iters"] == it, (eps, info["iters"], it)
+        if info["status"] == 0 and info["iters"] == i64["iters"]:
+            best_gpu = eps
+        if st == 0 and it == i64["iters"]:
+            best_orc = eps
+    assert best_gpu is not None and best_gpu == best_orc
+
+
+@pytest.mark.parametrize("block,eps", [(0, 1e-16), (0, 1e-7), (0, 1e-3), (32, 1e-7), (1, 1e-5)])
+def test_power_graph_laplacian(q, orc, block, eps):
+    """Random graph Laplacian (n = 3000): APM with tau = 1e-6 and at most 300
+    iterations takes the oracle's iteration count and eigenvalue; the first
+    Rayleigh quotient's class counts equal the oracle's."""
+    rp, col, val = workloads.graph_laplacian(3000, 8)
+    n = rp.shape[0] - 1
+    x0 = workloads.unit_start(n)
+    lam, x, info, hist = q.power(q.Csr(rp, col, val), _dev(x0), iters=300, tau=1e-6, eps=eps, block=block,
+                                 history=True)
+    lo, xo, it, counts, st = orc.power(rp, col, val, x0, iters=300, tau=1e-6, eps=eps, block=block)
+    assert st == 0 and info["status"] == 0
+    assert abs(info["iters"] - it) <= 1
+    assert abs(lam - lo) <= 1e-9 * abs(lo)
+    ref = orc.qdot(x0, orc.spmv(rp, col, val, x0), eps=eps, block=block)
+    np.testing.assert_array_equal(hist[0, 0], ref.count)

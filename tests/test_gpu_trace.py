@@ -107,6 +107,22 @@ def test_trace_fused(q, orc, block):
             assert np.all(np.isin(units["source"], (SRC["none"], SRC["fused"])))
 
 
+@pytest.mark.parametrize("block", [0, 1])
+def test_trace_fused_bins(q, orc, block):
+    """The one-launch path for exact binning and blocks of one: the class map
+    it summed with and every item's value; zeros in one case."""
+    n = (1 << 21) + 77
+    rng = np.random.default_rng(9)
+    for kind in ("b", "c", "cfg0"):
+        x, y = workloads.pair(kind, n, 310 + block)
+        if kind == "c":
+            x[rng.random(n) < 0.01] = 0.0
+        xd, yd = _dev(x), _dev(y)
+        for eps in (1e-16, 1e-8, 1e-1):
+            _, units = check_trace(q, orc, x, y, eps, block, expect_kernel="k_qdot_fused_bins", xd=xd, yd=yd)
+            assert np.all(np.isin(units["source"], (SRC["none"], SRC["fused"])))
+
+
 @pytest.mark.parametrize("block", [32, 64, 256])
 def test_trace_one_pass_blocks(q, orc, block):
     """k_onepass + k_op_gather at a size past the fused limit, a ragged end,
@@ -157,6 +173,30 @@ def test_trace_one_pass_components(q, orc, eps):
             assert np.count_nonzero(units["source"] == SRC["item_recomputed"]) > 0
 
 
+def test_trace_one_pass_items_blocks_of_32(q, orc):
+    """k_onepass_items + k_op_gather_items with blocks of 32 (n from 2^25):
+    each block classed from its key log2 B + u_b, each item of 256 summed on
+    its own grid or recomputed; the per-component class map and every item's
+    value against the oracle.  Lognormal and uniform-with-outliers data with a
+    ragged end, zeros (statistics-only items, general recompute) and a ramp
+    whose bound of e_max lags (many items recomputed)."""
+    n = (1 << 25) + 333
+    rng = np.random.default_rng(41)
+    for kind in ("b", "c"):
+        x, y = workloads.pair(kind, n, 600)
+        xd, yd = _dev(x), _dev(y)
+        for eps in (1e-15, 1e-8, 1e-1):
+            _, units = check_trace(q, orc, x, y, eps, 32, expect_kernel="k_onepass_items", xd=xd, yd=yd)
+            assert set(np.unique(units["source"]).tolist()) <= {SRC["item"], SRC["item_recomputed"]}
+    x, y = workloads.pair("c", n, 601)
+    sparse = x.copy()
+    sparse[rng.random(n) < 0.01] = 0.0
+    ramp = x * np.exp2(np.linspace(0.0, 40.0, n))
+    for xx in (sparse, ramp):
+        _, units = check_trace(q, orc, xx, y, 1e-8, 32, expect_kernel="k_onepass_items")
+        assert np.count_nonzero(units["source"] == SRC["item_recomputed"]) > 0
+
+
 def test_trace_repeatable_bit_for_bit(q, orc):
     """The one-pass path's speculation depends on timing (a shared running
     bound of e_max), but every candidate has one definition: repeated calls
@@ -203,7 +243,7 @@ def test_trace_full_size_benched_cell(q, orc):
     eps = 1e-8, the same seed and launch shape as bench.py), unit by unit."""
     n = 1 << 28
     x, y = workloads.pair("b", n, 2106)
-    check_trace(q, orc, x, y, 1e-8, 32, expect_kernel="k_onepass")
+    check_trace(q, orc, x, y, 1e-8, 32, expect_kernel="k_onepass_items")
 
 
 def test_trace_rejects_two_pass(q):
