@@ -837,9 +837,21 @@ def run_backward(args, rank, world, local, dist, lib):
     dist.barrier()
     clk = clocks.stop()
     ms = dist.max(t0.elapsed_time(t1)) / args.steps
+    # the forward alone (batched launch, no graph recorded), for the split
+    with torch.no_grad():
+        for _ in range(2):
+            autograd.qdot_batch_fn(X, Y, eps=args.eps, block=args.block)
+        t0.record()
+        for _ in range(args.steps):
+            autograd.qdot_batch_fn(X, Y, eps=args.eps, block=args.block)
+        t1.record()
+        torch.cuda.synchronize()
+    ms_fwd = t0.elapsed_time(t1) / args.steps
     # forward 16 B/elem + backward 32 B/elem
     total = Bn * L
     return {
+        "forward_ms": ms_fwd, "forward_gbs": 16.0 * total / (ms_fwd * 1e-3) / 1e9,
+        "backward_ms": ms - ms_fwd, "backward_gbs": 32.0 * total / max((ms - ms_fwd) * 1e-3, 1e-12) / 1e9,
         "metric": "qdot forward+backward GB/s", "value": world * 48.0 * total / (ms * 1e-3) / 1e9, "unit": "GB/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -101,6 +101,13 @@ PathChoice choose_path(int64_t n, const qdot_params* p, bool al16) {
   if (p->block == 1 && n < kOnePassMinN1) one = false;
   const bool fused = fused_supported(n, p, al16);
   if (p->path == QDOT_PATH_FUSED) return fused ? kFused : (one ? kOnePass : kTwoPass);
+  // exact binning and blocks of one: the fused launch reads HBM once, but its
+  // grid barriers cost more than the two-pass path's second read, which L2
+  // serves at these sizes (measured per call in CUDA graphs, n = 2^16 .. 2^22:
+  // 13.5 / 28 / 45 us fused against 13.7 / 23 / 33 us two-pass for blocks of
+  // one; 20 / 36 / 53 against 17 / 27 / 37 for exact binning), so AUTO keeps
+  // the two passes there and QDOT_PATH_FUSED selects the fused launch
+  if (p->block <= 1) return one ? kOnePass : kTwoPass;
   return fused ? kFused : (one ? kOnePass : kTwoPass);
 }
 

@@ -15,14 +15,18 @@
 // operands it reads anyway: 32 bytes of traffic per component (read x, y;
 // write gx, gy) and no per-component map in memory.
 //
-// Layout: a warp walks rows of 256 consecutive components; lane l owns
-// components row*256 + 8l + [0, 8).  Blocks of B <= 8 components sit inside a
-// lane, blocks of 16 <= B <= 256 span B/8 lanes (segmented shuffles); larger
-// blocks take one CTA each (the block is read twice, the second time mostly
-// from L2).
+// Layout: a warp walks items of 256 consecutive components.  With 16-byte
+// aligned arrays, exact binning, blocks of one and blocks of 16 .. 256 use the
+// forward kernels' item layout (k_backward_items, k_backward_batched_items:
+// every warp-wide 16-byte access covers whole sectors).  Otherwise, and for
+// blocks of 2 .. 8, lane l owns components row*256 + 8l + [0, 8): blocks of
+// B <= 8 components sit inside a lane, blocks of 16 <= B <= 256 span B/8
+// lanes (segmented shuffles).  Larger blocks take one CTA each (the block is
+// read twice, the second time mostly from L2).
 #include <algorithm>
 #include <string>
 
+#include "qdot_chunk.cuh"
 #include "qdot_common.cuh"
 #include "qdot_internal.h"
 
@@ -247,9 +251,8 @@ __global__ void __launch_bounds__(kBwThreads) k_backward_blocks(const double* __
   }
 }
 
-// Batched: problem j's rows follow the rows of problems 0..j-1 (row_start,
-// from k_bw_plan); a warp finds its problem by binary search.  Blocked
-// binning, class from the forward's (e_max, f) of each problem.
+// Batched: the first row (item of 256 components) of every problem, an
+// exclusive scan of ceil(n_j / 256) in row_start[0 .. count].
 __global__ void k_bw_plan(const int64_t* __restrict__ ns, int count, long long* __restrict__ row_start) {
   // one CTA of 1024 threads: exclusive scan of ceil(n_j / 256)
   __shared__ long long s_tot[1024];
@@ -273,8 +276,141 @@ __global__ void k_bw_plan(const int64_t* __restrict__ ns, int count, long long* 
   if (threadIdx.x == 1023) row_start[count] = s_tot[1023];
 }
 
-template <int LOG2B>
-__global__ void __launch_bounds__(kBwThreads, 4) k_backward_batched(
+// ---------------------------------------------------------------------------
+// Coalesced kernels (16-byte aligned x, y, gx, gy): warp items of 256
+// components in the forward kernels' layout (qdot_chunk.cuh).  Lane l holds
+// components item_offset<LB>(l, j), read and written as four 16-byte pieces
+// of each array, so every warp-wide access covers whole 32-byte sectors
+// (the layout above, 8 consecutive components per lane, touches each sector
+// from two instructions).  LB = 8 for exact binning and blocks of one (class
+// per component); LB = log2 B for blocks of 16 .. 256 (class per block, the
+// block's L = B / 8 lanes reduce u_b and M_b by shuffles).
+// ---------------------------------------------------------------------------
+
+// Item `item` of (x, y): 16-byte loads for a whole item when ALIGNED, else
+// (and at the vectors' end) one component at a time.
+template <int LB>
+__device__ __forceinline__ void bw_load(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                        long long item, int lane, bool aligned, chunk::Chunk& ch) {
+  if (aligned) {
+    chunk::load_item<LB>(x, y, n, item, lane, ch);
+    return;
+  }
+  const long long start = item * chunk::kItem;
+  ch.vmask = 0u;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const long long i = start + chunk::item_offset<LB>(lane, j);
+    const bool in = i < n;
+    ch.vmask |= in ? (1u << j) : 0u;
+    ch.x[j] = in ? (uint64_t)__double_as_longlong(x[i]) : 0ull;
+    ch.y[j] = in ? (uint64_t)__double_as_longlong(y[i]) : 0ull;
+  }
+}
+
+template <int LB>
+__device__ __forceinline__ void bw_store(double* __restrict__ p, long long n, long long item, int lane, bool aligned,
+                                         const double (&v)[8]) {
+  if (!p) return;
+  constexpr int L = chunk::Map<LB>::L;
+  const long long start = item * chunk::kItem;
+  if (aligned && start + chunk::kItem <= n) {
+    double2* p2 = reinterpret_cast<double2*>(p + start + chunk::item_offset<LB>(lane, 0));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) __stcs(p2 + L * j, make_double2(v[2 * j], v[2 * j + 1]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long i = start + chunk::item_offset<LB>(lane, j);
+      if (i < n) __stcs(p + i, v[j]);
+    }
+  }
+}
+
+// Classes of a lane's 8 components of one item: by the component's key
+// (BLOCKS false) or by the block key ceil(log2 M_b) + u_b (BLOCKS true; every
+// lane of the warp must call this together).  Components outside the vectors
+// or with a zero factor are ZERO.
+template <int LB, bool BLOCKS, typename ClassOf>
+__device__ __forceinline__ void item_classes(const chunk::Chunk& ch, ClassOf cls_of, int (&cls)[8]) {
+  int key[8];
+  bool nz[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    nz[j] = ((ch.vmask >> j) & 1u) && !is_zero(ch.x[j]) && !is_zero(ch.y[j]);
+    key[j] = nz[j] ? exponent_of(ch.x[j]) + exponent_of(ch.y[j]) : kNoKey;
+  }
+  if constexpr (!BLOCKS) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) cls[j] = nz[j] ? cls_of(key[j]) : kZero;
+  } else {
+    constexpr int L = chunk::Map<LB>::L;
+    int u = kNoKey;
+    unsigned M = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      u = max(u, key[j]);
+      M += nz[j] ? 1u : 0u;
+    }
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+      u = max(u, __shfl_xor_sync(0xffffffffu, u, o));
+      M += __shfl_xor_sync(0xffffffffu, M, o);
+    }
+    const int bc = M ? cls_of(ceil_log2_u32(M) + u) : kZero;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) cls[j] = nz[j] ? bc : kZero;
+  }
+}
+
+template <int LB>
+__device__ __forceinline__ void item_grads(const chunk::Chunk& ch, const int (&cls)[8], double g, long long n,
+                                           long long item, int lane, bool aligned, double* __restrict__ gx,
+                                           double* __restrict__ gy) {
+  double a[8];
+  if (gx) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = g * quantized_value(ch.y[j], cls[j]);
+    bw_store<LB>(gx, n, item, lane, aligned, a);
+  }
+  if (gy) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = g * quantized_value(ch.x[j], cls[j]);
+    bw_store<LB>(gy, n, item, lane, aligned, a);
+  }
+}
+
+// Single problem, exact binning or B in {1, 16, ..., 256}: class from the
+// forward's table.
+template <int LB, bool BLOCKS>
+__global__ void __launch_bounds__(kBwThreads, 4) k_backward_items(const double* __restrict__ x,
+                                                              const double* __restrict__ y, long long n,
+                                                              const qdot_selection* __restrict__ sel,
+                                                              const double* __restrict__ g, double* __restrict__ gx,
+                                                              double* __restrict__ gy) {
+  __shared__ uint8_t lut[kKeyCount];
+  for (int k = threadIdx.x; k < kKeyCount; k += kBwThreads) lut[k] = sel->cls[k];
+  __syncthreads();
+  const double gv = *g;
+  const int lane = threadIdx.x & 31;
+  const long long nitems = (n + chunk::kItem - 1) / chunk::kItem;
+  const long long nwarps = (long long)gridDim.x * (kBwThreads / 32);
+  auto cls_of = [&](int k) { return (int)lut[lut_index(k)]; };
+  for (long long it = (long long)blockIdx.x * (kBwThreads / 32) + (threadIdx.x >> 5); it < nitems; it += nwarps) {
+    chunk::Chunk ch;
+    chunk::load_item<LB>(x, y, n, it, lane, ch);
+    int cls[8];
+    item_classes<LB, BLOCKS>(ch, cls_of, cls);
+    item_grads<LB>(ch, cls, gv, n, it, lane, true, gx, gy);
+  }
+}
+
+// Batched, blocks of 32 .. 256: problem j's items follow those of problems
+// 0 .. j-1 (row_start, rows of 256 = items).  Each warp takes one contiguous
+// range of items, finds its first problem by binary search and then walks
+// forward; class from the forward's (e_max, f) of each problem.
+template <int LB>
+__global__ void __launch_bounds__(kBwThreads, 4) k_backward_batched_items(
     const double* const* __restrict__ xs, const double* const* __restrict__ ys, const int64_t* __restrict__ ns,
     int count, const long long* __restrict__ row_start, const qdot_result* __restrict__ outs,
     const double* __restrict__ gs, double* const* __restrict__ gxs, double* const* __restrict__ gys, int mh,
@@ -282,13 +418,22 @@ __global__ void __launch_bounds__(kBwThreads, 4) k_backward_batched(
   const int lane = threadIdx.x & 31;
   const long long total = row_start[count];
   const long long nwarps = (long long)gridDim.x * (kBwThreads / 32);
-  for (long long r = (long long)blockIdx.x * (kBwThreads / 32) + (threadIdx.x >> 5); r < total; r += nwarps) {
-    int lo = 0, hi = count - 1;  // last j with row_start[j] <= r
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (row_start[mid] <= r) lo = mid; else hi = mid - 1;
+  const long long gw = (long long)blockIdx.x * (kBwThreads / 32) + (threadIdx.x >> 5);
+  const long long per = (total + nwarps - 1) / nwarps;
+  const long long r0 = gw * per, r1 = min(total, r0 + per);
+  if (r0 >= r1) return;  // warp-uniform
+  int lo = 0, hi = count - 1;  // last j with row_start[j] <= r0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row_start[mid] <= r0) lo = mid; else hi = mid - 1;
+  }
+  int j = lo;
+  long long jend = row_start[j + 1];
+  for (long long r = r0; r < r1; ++r) {
+    while (r >= jend) {  // next problem with items (empty ones have none)
+      ++j;
+      jend = row_start[j + 1];
     }
-    const int j = lo;
     const double* x = xs[j];
     const double* y = ys[j];
     double* gx = gxs ? gxs[j] : nullptr;
@@ -298,23 +443,27 @@ __global__ void __launch_bounds__(kBwThreads, 4) k_backward_batched(
     const bool ok = outs[j].status == QDOT_OK;
     const uintptr_t a = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) |
                         reinterpret_cast<uintptr_t>(gx) | reinterpret_cast<uintptr_t>(gy);
-    const long long base = (r - row_start[j]) * kBwRow + lane * kBwVec;
-    uint64_t xb[kBwVec] = {}, yb[kBwVec] = {};
+    const bool aligned = (a & 15u) == 0;
+    const long long item = r - row_start[j];
+    chunk::Chunk ch;
     if (ok) {
-      load8(x, base, n, xb, (a & 15u) == 0);
-      load8(y, base, n, yb, (a & 15u) == 0);
-    }
-    int cls[kBwVec];
-    auto cls_of = [&](int k) { return precision_of((long long)k - e_max - f + 1, mh, ms); };
-    lane_classes<LOG2B>(xb, yb, base, n, cls_of, cls);  // every lane joins the shuffles
-    if (ok) {
-      lane_grads(xb, yb, cls, gs[j], base, n, gx, gy, (a & 15u) == 0);
-    } else {  // no valid forward selection for this problem
-      double nan8[kBwVec];
+      bw_load<LB>(x, y, n, item, lane, aligned, ch);
+    } else {
+      ch.vmask = 0u;
 #pragma unroll
-      for (int k = 0; k < kBwVec; ++k) nan8[k] = __longlong_as_double(0x7FF8000000000000ll);
-      store8(gx, base, n, nan8, (a & 15u) == 0);
-      store8(gy, base, n, nan8, (a & 15u) == 0);
+      for (int k = 0; k < 8; ++k) ch.x[k] = ch.y[k] = 0ull;
+    }
+    int cls[8];
+    auto cls_of = [&](int k) { return precision_of((long long)k - e_max - f + 1, mh, ms); };
+    item_classes<LB, true>(ch, cls_of, cls);  // every lane joins the shuffles
+    if (ok) {
+      item_grads<LB>(ch, cls, gs[j], n, item, lane, aligned, gx, gy);
+    } else {  // no valid forward selection for this problem
+      double nan8[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) nan8[k] = __longlong_as_double(0x7FF8000000000000ll);
+      bw_store<LB>(gx, n, item, lane, aligned, nan8);
+      bw_store<LB>(gy, n, item, lane, aligned, nan8);
     }
   }
 }
@@ -364,7 +513,19 @@ qdot_status qdot_backward(const double* x, const double* y, int64_t n, const qdo
   const long long rows = (n + kBwRow - 1) / kBwRow;
   const int grid = bw_grid((rows + 7) / 8, 4);
   const int B = p->block;
-  switch (B) {
+  if (al16 && (B <= 1 || (B >= 16 && B <= 256))) {  // coalesced item layout
+    const long long items = (n + chunk::kItem - 1) / chunk::kItem;
+    const int gi = bw_grid((items + 7) / 8, 4);
+    switch (B) {
+      case 0:
+      case 1: k_backward_items<8, false><<<gi, kBwThreads, 0, st>>>(x, y, n, sel, g, gx, gy); break;
+      case 16: k_backward_items<4, true><<<gi, kBwThreads, 0, st>>>(x, y, n, sel, g, gx, gy); break;
+      case 32: k_backward_items<5, true><<<gi, kBwThreads, 0, st>>>(x, y, n, sel, g, gx, gy); break;
+      case 64: k_backward_items<6, true><<<gi, kBwThreads, 0, st>>>(x, y, n, sel, g, gx, gy); break;
+      case 128: k_backward_items<7, true><<<gi, kBwThreads, 0, st>>>(x, y, n, sel, g, gx, gy); break;
+      default: k_backward_items<8, true><<<gi, kBwThreads, 0, st>>>(x, y, n, sel, g, gx, gy); break;
+    }
+  } else switch (B) {
     case 0:
     case 1: launch_rows<-1>(al16, grid, x, y, n, sel, g, gx, gy, st); break;
     case 2: launch_rows<1>(al16, grid, x, y, n, sel, g, gx, gy, st); break;
@@ -429,10 +590,10 @@ qdot_status qdot_batched_backward(const double* const* xs, const double* const* 
   const int grid = grid_ctas > 0 ? grid_ctas : bw_grid(1ll << 40, 4);
   k_bw_plan<<<1, 1024, 0, st>>>(ns, count, row_start);
   switch (p->block) {
-    case 32: k_backward_batched<5><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;
-    case 64: k_backward_batched<6><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;
-    case 128: k_backward_batched<7><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;
-    default: k_backward_batched<8><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;
+    case 32: k_backward_batched_items<5><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;
+    case 64: k_backward_batched_items<6><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;
+    case 128: k_backward_batched_items<7><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;
+    default: k_backward_batched_items<8><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -64,12 +64,10 @@ def test_stream_kernel_names(lib):
     assert name((1 << 25) - 1, 32) == b"k_onepass" and name(1 << 24, 32) == b"k_onepass"
     assert name(1 << 20, 32) in (b"k_onepass", b"k_qdot_fused")
     assert name(1 << 28, 64) == b"k_onepass" and name(1 << 28, 256) == b"k_onepass"
-    # blocks of one and exact binning: one fused launch where the resident grid
-    # covers the vectors (a device is needed to know), else two passes; blocks
-    # of one take item records from 2^24 on
+    # blocks of one and exact binning: two passes (the fused launch only when
+    # asked for); blocks of one take item records from 2^24 on
     assert name(1 << 28, 1) == b"k_onepass_items"
-    assert name(1 << 20, 1) in (b"k_apply_fast", b"k_qdot_fused_bins")
-    assert name(1 << 20, 0) in (b"k_apply_fast", b"k_qdot_fused_bins")
+    assert name(1 << 20, 1) == b"k_apply_fast" and name(1 << 20, 0) == b"k_apply_fast"
     assert name(1 << 23, 1) == b"k_apply_fast"
     assert name(1 << 28, 0) == b"k_apply_fast" and name(1 << 28, 8) == b"k_apply_fast"
     assert name(1 << 28, 32, al16=0) == b"k_apply_fast"  # 8-byte aligned inputs

@@ -99,6 +99,8 @@ def _rows(B, L, seed):
 
 @pytest.mark.parametrize("block", [32, 64, 256])
 def test_batched_backward_matches_oracle(ag, orc, block):
+    """Rows of 4098 components: every row 16-byte aligned (the batched forward
+    requires it), a ragged last item of 2 components."""
     import torch
     X, Y = _rows(24, 4098, 91)
     Xt, Yt = _dev(X), _dev(Y)

@@ -309,24 +309,27 @@ def test_fused_path(q, orc, block):
 
 @pytest.mark.parametrize("block", [0, 1])
 def test_fused_bins_path(q, orc, block):
-    """Exact binning and blocks of one in one cooperative launch: statistics
-    (and the bin counts M_k) from one read, the sums from a second read out of
-    L2.  Every distribution, the 65536-component configuration of +-10^U(-8,0)
-    values, the solvers' sizes and the largest n the grid covers; past it the
-    call takes two passes."""
+    """Exact binning and blocks of one in one cooperative launch (selected with
+    path="fused"): statistics and the bin counts M_k from one read, the sums
+    from a second read out of L2.  Every distribution, the 65536-component
+    configuration of +-10^U(-8,0) values, the solvers' sizes and the largest n
+    the grid covers; past it the call takes two passes.  AUTO keeps two passes
+    for these modes (faster at every size measured)."""
     import ctypes
     lib = q.load()
-    p = q.params(1e-8, block, 1, 0, "auto")
+    p = q.params(1e-8, block, 1, 0, "fused")
+    pa = q.params(1e-8, block, 1, 0, "auto")
     for n in (257, 65536, 1 << 20, 2097152 + 3, 3 * 10**6 + 1):
         assert lib.qdot_select_path(n, ctypes.byref(p), 1) == 4  # QDOT_PATH_FUSED
         assert lib.qdot_kernel_launches(n, ctypes.byref(p), 1) == 1
         assert lib.qdot_stream_kernel(n, ctypes.byref(p), 1) == b"k_qdot_fused_bins"
+        assert lib.qdot_select_path(n, ctypes.byref(pa), 1) == 1  # AUTO: two passes
         for kind in ("a", "b", "c", "cfg0"):
             if n > 65536 and kind in ("a", "cfg0"):
                 continue
             x, y = workloads.pair(kind, n, 70 + block + n % 97)
             for eps in (1e-16, 1e-8, 1e-3, 0.5):
-                _check(q, orc, x, y, eps, block, explain=False)
+                _check(q, orc, x, y, eps, block, explain=False, path="fused")
     assert lib.qdot_select_path(1 << 23, ctypes.byref(p), 1) == 1  # two passes
 
 
@@ -346,7 +349,7 @@ def test_fused_bins_edge_cases(q, orc):
     for xx, yy in cases:
         for block in (0, 1):
             for eps in (1e-16, 1e-8, 2.0**-8, 4.0, 0.5):
-                _check(q, orc, xx, yy, eps, block, explain=False)
+                _check(q, orc, xx, yy, eps, block, explain=False, path="fused")
 
 
 def test_fused_bins_matches_item_path_bits(q, orc):

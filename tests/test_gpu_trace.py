@@ -119,7 +119,8 @@ def test_trace_fused_bins(q, orc, block):
             x[rng.random(n) < 0.01] = 0.0
         xd, yd = _dev(x), _dev(y)
         for eps in (1e-16, 1e-8, 1e-1):
-            _, units = check_trace(q, orc, x, y, eps, block, expect_kernel="k_qdot_fused_bins", xd=xd, yd=yd)
+            _, units = check_trace(q, orc, x, y, eps, block, path="fused", expect_kernel="k_qdot_fused_bins",
+                                   xd=xd, yd=yd)
             assert np.all(np.isin(units["source"], (SRC["none"], SRC["fused"])))
 
 
