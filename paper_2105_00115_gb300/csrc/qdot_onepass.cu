@@ -703,10 +703,13 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
 
 // Gather of item records: an item whose bound e_lo was e_max, and f_spec f, adds
 // its record; any other item is recomputed with the final classes.  The CTA
-// takes 256 items at a time, one per thread, and its warps recompute the
-// rejected ones of each round together.  Items are dealt to the CTAs in turn
-// (item i to CTA i mod grid): the rejected items are mostly every warp's
-// first few, at the start of the vectors, and this spreads them evenly.
+// takes kGatherPer x 256 items per round, kGatherPer per thread with
+// independent loads, and its warps recompute the rejected ones of each round
+// together.  Items are dealt to the CTAs in turn (item i to CTA i mod grid):
+// the rejected items are mostly every warp's first few, at the start of the
+// vectors, and this spreads them evenly.
+constexpr int kGatherPer = 4;
+
 template <int LOG2B>
 __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __restrict__ isum,
                                                      const unsigned long long* __restrict__ imeta, long long nitems,
@@ -716,7 +719,7 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
                                                      long long n, qdot_result* __restrict__ out,
                                                      qdot_trace_unit* __restrict__ trace, uint8_t* __restrict__ tcls) {
   __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
-  __shared__ long long s_qitem[256];
+  __shared__ long long s_qitem[256 * kGatherPer];
   __shared__ int s_nqueue;
   for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
     reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
@@ -732,38 +735,47 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
   long long acc_hi = 0;
   unsigned long long c[5] = {0, 0, 0, 0, 0};
   const long long G = gridDim.x;
-  for (long long q0 = 0; ok && q0 * G + blockIdx.x < nitems; q0 += blockDim.x) {
-    const long long i = (q0 + threadIdx.x) * G + blockIdx.x;
-    if (i < nitems) {
-      const unsigned long long m = imeta[i];
-      const long long v = isum[i];
-      if (f_exact && !(m & kItemRecompute) && (unsigned)((m >> 12) & 0xFFFu) == anchor) {
-        const unsigned nh = (unsigned)(m >> 24) & 0x1FFu, ns = (unsigned)(m >> 33) & 0x1FFu,
-                       nd = (unsigned)(m >> 42) & 0x1FFu;
+  const long long T = blockDim.x;
+  for (long long q0 = 0; ok && q0 * G + blockIdx.x < nitems; q0 += T * kGatherPer) {
+    unsigned long long m[kGatherPer];
+    long long v[kGatherPer];
+#pragma unroll
+    for (int k = 0; k < kGatherPer; ++k) {  // independent loads first
+      const long long i = (q0 + threadIdx.x + k * T) * G + blockIdx.x;
+      m[k] = i < nitems ? imeta[i] : 0ull;
+      v[k] = i < nitems ? isum[i] : 0ll;
+    }
+#pragma unroll
+    for (int k = 0; k < kGatherPer; ++k) {
+      const long long i = (q0 + threadIdx.x + k * T) * G + blockIdx.x;
+      if (i >= nitems) continue;
+      if (f_exact && !(m[k] & kItemRecompute) && (unsigned)((m[k] >> 12) & 0xFFFu) == anchor) {
+        const unsigned nh = (unsigned)(m[k] >> 24) & 0x1FFu, ns = (unsigned)(m[k] >> 33) & 0x1FFu,
+                       nd = (unsigned)(m[k] >> 42) & 0x1FFu;
         c[kHalf] += nh;
         c[kSingle] += ns;
         c[kDouble] += nd;
         c[kPerf] += kItem - nh - ns - nd;
-        const int sh = (int)(m & 0xFFFu) - 2046 - 52 - lsb;  // <= L - 52
+        const int sh = (int)(m[k] & 0xFFFu) - 2046 - 52 - lsb;  // <= L - 52
         const int sl = min(max(sh, 0), 63), sr = min(max(-sh, 0), 63);
-        const long long wv = v >> sr;
+        const long long wv = v[k] >> sr;
         const unsigned long long lo = (unsigned long long)wv << sl;
         acc_lo += lo;
         acc_hi += ((wv >> 1) >> (63 - sl)) + (acc_lo < lo ? 1 : 0);
-        if (trace) trace[i] = qdot_trace_unit{v, (int)(m & 0xFFFu) - 2046 - 52, 255, (uint8_t)QDOT_TRACE_ITEM, 0};
+        if (trace) trace[i] = qdot_trace_unit{v[k], (int)(m[k] & 0xFFFu) - 2046 - 52, 255, (uint8_t)QDOT_TRACE_ITEM, 0};
       } else {
         ++c[4];
-        s_qitem[atomicAdd(&s_nqueue, 1)] = i;  // at most one per thread and round
+        s_qitem[atomicAdd(&s_nqueue, 1)] = i;  // at most kGatherPer per thread and round
       }
     }
     __syncthreads();
     const int nq = s_nqueue;
     for (int qi = w; qi < nq; qi += (int)(blockDim.x >> 5)) {
       int u;
-      const long long v = recompute_item_fast<LOG2B>(x, y, n, s_qitem[qi], s_lut, lane, &u, c, tcls);
-      if (lane == 0 && u != kNone) acc += candidate_to_fixed(v, kSingle, u, 8, lsb);  // grid 2^(u - 52)
+      const long long vv = recompute_item_fast<LOG2B>(x, y, n, s_qitem[qi], s_lut, lane, &u, c, tcls);
+      if (lane == 0 && u != kNone) acc += candidate_to_fixed(vv, kSingle, u, 8, lsb);  // grid 2^(u - 52)
       if (lane == 0 && trace)
-        trace[s_qitem[qi]] = qdot_trace_unit{u != kNone ? v : 0ll, u != kNone ? u - 52 : 0, 255,
+        trace[s_qitem[qi]] = qdot_trace_unit{u != kNone ? vv : 0ll, u != kNone ? u - 52 : 0, 255,
                                              (uint8_t)QDOT_TRACE_ITEM_RECOMPUTED, 0};
     }
     __syncthreads();
