@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--block", type=int, default=32)
     ap.add_argument("--eps", type=float, default=1e-8)
     ap.add_argument("--path", default="auto", choices=["auto", "two_pass", "one_pass"])
+    ap.add_argument("--seed", type=int, default=2106,
+                    help="data seed of the single-qdot workload (the speculative paths' speed depends on where "
+                         "the largest product lies)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -244,7 +247,7 @@ def run_reference(args, rank, world):
     import workloads
     oracle.build()
     m = min(args.n, 1 << 22)
-    x, y = workloads.pair(args.dist, m, 2106)
+    x, y = workloads.pair(args.dist, m, args.seed)
     for _ in range(args.warmup):
         oracle.qdot(x, y, eps=args.eps, block=args.block)
     times = []
@@ -273,7 +276,7 @@ def workload_config(args):
     return {"workload": f"single qdot, n=2^{args.n.bit_length() - 1}, {DIST_NAMES[args.dist]}, block={args.block}, "
                         f"eps={args.eps:g}",
             "n": args.n, "distribution": DIST_NAMES[args.dist], "block": args.block, "eps": args.eps,
-            "split_budget": 1, "mant_reading": 0, "seed": 2106,
+            "split_budget": 1, "mant_reading": 0, "seed": args.seed,
             "l2": "inputs 4 GiB per step > 129 MB L2 (no flush needed)" if args.n >= (1 << 24)
                   else "inputs smaller than L2"}
 
@@ -931,7 +934,7 @@ def main():
         dist.close()
         return
     n = args.n
-    x, y = workloads.pair(args.dist, n, 2106 + rank)
+    x, y = workloads.pair(args.dist, n, args.seed + rank)
     if args.sweep:
         xd = torch.from_numpy(x).cuda()
         yd = torch.from_numpy(y).cuda()

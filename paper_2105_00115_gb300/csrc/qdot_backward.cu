@@ -363,47 +363,11 @@ __device__ __forceinline__ void item_classes(const chunk::Chunk& ch, ClassOf cls
   }
 }
 
-// q_c(v) for a normal finite v (exponent field 1 .. 2046) without branches:
-// the bit pattern with its significand rounded to nearest-even at bit 42
-// (HALF) or 29 (SINGLE), a carry moving into the exponent field (which can
-// reach 0x7FF only with a zero fraction: +-Inf, as quantized_value gives);
-// v itself for DOUBLE; 0 for PERF and ZERO.
-__device__ __forceinline__ double quantized_normal(uint64_t v, int cls) {
-  const int k = cls == kHalf ? 42 : 29;
-  const uint64_t r = (v + ((1ull << (k - 1)) - 1ull) + ((v >> k) & 1ull)) & ~((1ull << k) - 1ull);
-  const uint64_t q = cls == kDouble ? v : ((cls == kHalf || cls == kSingle) ? r : 0ull);
-  return __longlong_as_double((long long)q);
-}
-
-// Whether every component of the lane's chunk has normal finite x and y.
-__device__ __forceinline__ bool chunk_all_normal(const chunk::Chunk& ch) {
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    ok &= (unsigned)(((ch.x[j] >> 52) & 0x7FFu) - 1u) < 2046u;
-    ok &= (unsigned)(((ch.y[j] >> 52) & 0x7FFu) - 1u) < 2046u;
-  }
-  return ok;
-}
-
 template <int LB>
 __device__ __forceinline__ void item_grads(const chunk::Chunk& ch, const int (&cls)[8], double g, long long n,
                                            long long item, int lane, bool aligned, double* __restrict__ gx,
                                            double* __restrict__ gy) {
   double a[8];
-  if (__all_sync(0xffffffffu, chunk_all_normal(ch))) {  // warp-uniform: no branch per component
-    if (gx) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] = g * quantized_normal(ch.y[j], cls[j]);
-      bw_store<LB>(gx, n, item, lane, aligned, a);
-    }
-    if (gy) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] = g * quantized_normal(ch.x[j], cls[j]);
-      bw_store<LB>(gy, n, item, lane, aligned, a);
-    }
-    return;
-  }
   if (gx) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) a[j] = g * quantized_value(ch.y[j], cls[j]);
@@ -419,7 +383,7 @@ __device__ __forceinline__ void item_grads(const chunk::Chunk& ch, const int (&c
 // Single problem, exact binning or B in {1, 16, ..., 256}: class from the
 // forward's table.
 template <int LB, bool BLOCKS>
-__global__ void __launch_bounds__(kBwThreads, 2) k_backward_items(const double* __restrict__ x,
+__global__ void __launch_bounds__(kBwThreads, 4) k_backward_items(const double* __restrict__ x,
                                                               const double* __restrict__ y, long long n,
                                                               const qdot_selection* __restrict__ sel,
                                                               const double* __restrict__ g, double* __restrict__ gx,
@@ -432,15 +396,12 @@ __global__ void __launch_bounds__(kBwThreads, 2) k_backward_items(const double* 
   const long long nitems = (n + chunk::kItem - 1) / chunk::kItem;
   const long long nwarps = (long long)gridDim.x * (kBwThreads / 32);
   auto cls_of = [&](int k) { return (int)lut[lut_index(k)]; };
-  long long it = (long long)blockIdx.x * (kBwThreads / 32) + (threadIdx.x >> 5);
-  chunk::Chunk cur, nxt;
-  if (it < nitems) chunk::load_item<LB>(x, y, n, it, lane, cur);
-  for (; it < nitems; it += nwarps) {
-    if (it + nwarps < nitems) chunk::load_item<LB>(x, y, n, it + nwarps, lane, nxt);  // in flight meanwhile
+  for (long long it = (long long)blockIdx.x * (kBwThreads / 32) + (threadIdx.x >> 5); it < nitems; it += nwarps) {
+    chunk::Chunk ch;
+    chunk::load_item<LB>(x, y, n, it, lane, ch);
     int cls[8];
-    item_classes<LB, BLOCKS>(cur, cls_of, cls);
-    item_grads<LB>(cur, cls, gv, n, it, lane, true, gx, gy);
-    cur = nxt;
+    item_classes<LB, BLOCKS>(ch, cls_of, cls);
+    item_grads<LB>(ch, cls, gv, n, it, lane, true, gx, gy);
   }
 }
 
@@ -449,7 +410,7 @@ __global__ void __launch_bounds__(kBwThreads, 2) k_backward_items(const double* 
 // range of items, finds its first problem by binary search and then walks
 // forward; class from the forward's (e_max, f) of each problem.
 template <int LB>
-__global__ void __launch_bounds__(kBwThreads, 2) k_backward_batched_items(
+__global__ void __launch_bounds__(kBwThreads, 4) k_backward_batched_items(
     const double* const* __restrict__ xs, const double* const* __restrict__ ys, const int64_t* __restrict__ ns,
     int count, const long long* __restrict__ row_start, const qdot_result* __restrict__ outs,
     const double* __restrict__ gs, double* const* __restrict__ gxs, double* const* __restrict__ gys, int mh,
@@ -466,54 +427,37 @@ __global__ void __launch_bounds__(kBwThreads, 2) k_backward_batched_items(
     const int mid = (lo + hi + 1) >> 1;
     if (row_start[mid] <= r0) lo = mid; else hi = mid - 1;
   }
-  // problem j of row r (rows increase, so j only moves forward; empty
-  // problems have no rows and are skipped)
-  auto problem_of = [&](long long r, int& jj, long long& jend) {
-    while (r >= jend) {
-      ++jj;
-      jend = row_start[jj + 1];
-    }
-  };
-  auto load_row = [&](long long r, int jj, chunk::Chunk& ch) {
-    const double* x = xs[jj];
-    const double* y = ys[jj];
-    const uintptr_t a = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) |
-                        reinterpret_cast<uintptr_t>(gxs ? gxs[jj] : nullptr) |
-                        reinterpret_cast<uintptr_t>(gys ? gys[jj] : nullptr);
-    if (outs[jj].status == QDOT_OK) {
-      bw_load<LB>(x, y, ns[jj], r - row_start[jj], lane, (a & 15u) == 0, ch);
-    } else {
-      ch.vmask = 0u;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) ch.x[k] = ch.y[k] = 0ull;
-    }
-  };
   int j = lo;
   long long jend = row_start[j + 1];
-  problem_of(r0, j, jend);
-  int jn = j;
-  long long jnend = jend;
-  chunk::Chunk cur, nxt;
-  load_row(r0, j, cur);
   for (long long r = r0; r < r1; ++r) {
-    if (r + 1 < r1) {  // the next row's loads are in flight meanwhile
-      problem_of(r + 1, jn, jnend);
-      load_row(r + 1, jn, nxt);
+    while (r >= jend) {  // next problem with items (empty ones have none)
+      ++j;
+      jend = row_start[j + 1];
     }
+    const double* x = xs[j];
+    const double* y = ys[j];
     double* gx = gxs ? gxs[j] : nullptr;
     double* gy = gys ? gys[j] : nullptr;
     const long long n = ns[j];
     const int e_max = outs[j].e_max, f = outs[j].f;
     const bool ok = outs[j].status == QDOT_OK;
-    const uintptr_t a = reinterpret_cast<uintptr_t>(xs[j]) | reinterpret_cast<uintptr_t>(ys[j]) |
+    const uintptr_t a = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) |
                         reinterpret_cast<uintptr_t>(gx) | reinterpret_cast<uintptr_t>(gy);
     const bool aligned = (a & 15u) == 0;
     const long long item = r - row_start[j];
+    chunk::Chunk ch;
+    if (ok) {
+      bw_load<LB>(x, y, n, item, lane, aligned, ch);
+    } else {
+      ch.vmask = 0u;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ch.x[k] = ch.y[k] = 0ull;
+    }
     int cls[8];
     auto cls_of = [&](int k) { return precision_of((long long)k - e_max - f + 1, mh, ms); };
-    item_classes<LB, true>(cur, cls_of, cls);  // every lane joins the shuffles
+    item_classes<LB, true>(ch, cls_of, cls);  // every lane joins the shuffles
     if (ok) {
-      item_grads<LB>(cur, cls, gs[j], n, item, lane, aligned, gx, gy);
+      item_grads<LB>(ch, cls, gs[j], n, item, lane, aligned, gx, gy);
     } else {  // no valid forward selection for this problem
       double nan8[8];
 #pragma unroll
@@ -521,9 +465,6 @@ __global__ void __launch_bounds__(kBwThreads, 2) k_backward_batched_items(
       bw_store<LB>(gx, n, item, lane, aligned, nan8);
       bw_store<LB>(gy, n, item, lane, aligned, nan8);
     }
-    cur = nxt;
-    j = jn;
-    jend = jnend;
   }
 }
 
@@ -574,7 +515,7 @@ qdot_status qdot_backward(const double* x, const double* y, int64_t n, const qdo
   const int B = p->block;
   if (al16 && (B <= 1 || (B >= 16 && B <= 256))) {  // coalesced item layout
     const long long items = (n + chunk::kItem - 1) / chunk::kItem;
-    const int gi = bw_grid((items + 7) / 8, 2);  // the item kernels fit 2 CTAs per SM
+    const int gi = bw_grid((items + 7) / 8, 4);
     switch (B) {
       case 0:
       case 1: k_backward_items<8, false><<<gi, kBwThreads, 0, st>>>(x, y, n, sel, g, gx, gy); break;
@@ -646,7 +587,7 @@ qdot_status qdot_batched_backward(const double* const* xs, const double* const* 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   long long* row_start = static_cast<long long*>(ws);
   const int mh = p->mant_reading ? 11 : 10, ms = p->mant_reading ? 24 : 23;
-  const int grid = grid_ctas > 0 ? grid_ctas : bw_grid(1ll << 40, 2);  // 2 resident CTAs per SM
+  const int grid = grid_ctas > 0 ? grid_ctas : bw_grid(1ll << 40, 4);
   k_bw_plan<<<1, 1024, 0, st>>>(ns, count, row_start);
   switch (p->block) {
     case 32: k_backward_batched_items<5><<<grid, kBwThreads, 0, st>>>(xs, ys, ns, count, row_start, outs, gs, gxs, gys, mh, ms); break;

@@ -198,6 +198,23 @@ def test_trace_one_pass_items_blocks_of_32(q, orc):
         assert np.count_nonzero(units["source"] == SRC["item_recomputed"]) > 0
 
 
+def test_trace_items_late_maximum(q, orc):
+    """Blocks of 32 and of one on item records when the largest product sits in
+    the last item: every earlier item was summed with a bound of e_max below
+    the final one and is summed again with the final classes; every item's
+    value and the class map must still be the oracle's."""
+    n = (1 << 25) + 256 * 7
+    x, y = workloads.pair("b", n, 602)
+    for spike in (2.0**3, 2.0**10):  # the last item's product lies 6 or 20 binades above the rest
+        xx, yy = x.copy(), y.copy()
+        xx[-3] = np.abs(x).max() * spike
+        yy[-3] = np.abs(y).max() * spike
+        xd, yd = _dev(xx), _dev(yy)
+        for block, eps in ((32, 1e-15), (32, 1e-8), (32, 1e-1), (1, 1e-8)):
+            _, units = check_trace(q, orc, xx, yy, eps, block, expect_kernel="k_onepass_items", xd=xd, yd=yd)
+            assert np.count_nonzero(units["source"] == SRC["item_recomputed"]) > units.size // 2
+
+
 def test_trace_repeatable_bit_for_bit(q, orc):
     """The one-pass path's speculation depends on timing (a shared running
     bound of e_max), but every candidate has one definition: repeated calls
