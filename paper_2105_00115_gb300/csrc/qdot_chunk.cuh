@@ -832,6 +832,12 @@ __device__ long long recompute_item(const double* __restrict__ x, const double* 
   return v;
 }
 
+template <int LOG2B>
+__device__ long long recompute_loaded_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                           long long item, const Chunk& ch, const uint8_t* __restrict__ lut,
+                                           int lane, int* u_out, unsigned long long (&c)[5],
+                                           uint8_t* __restrict__ tcls);
+
 // recompute_item() on the streaming kernel's arithmetic, for an item whose
 // components are all in range, nonzero, normal and finite: the lanes load it
 // in the streaming layout and quantize with the final classes from the table
@@ -842,9 +848,21 @@ __device__ long long recompute_item_fast(const double* __restrict__ x, const dou
                                          long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
                                          unsigned long long (&c)[5], uint8_t* __restrict__ tcls) {
   constexpr int LB = LOG2B ? LOG2B : 8;
-  constexpr int L = Map<LB>::L;
   Chunk ch;
   load_item<LB>(x, y, n, item, lane, ch);
+  return recompute_loaded_item<LOG2B>(x, y, n, item, ch, lut, lane, u_out, c, tcls);
+}
+
+// recompute_item_fast() on an item the warp has already loaded (in the
+// streaming layout, `ch`); an item that is not plain goes to recompute_item(),
+// which reads it again.
+template <int LOG2B>
+__device__ long long recompute_loaded_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                           long long item, const Chunk& ch, const uint8_t* __restrict__ lut,
+                                           int lane, int* u_out, unsigned long long (&c)[5],
+                                           uint8_t* __restrict__ tcls) {
+  constexpr int LB = LOG2B ? LOG2B : 8;
+  constexpr int L = Map<LB>::L;
   int key[8];
   int cmax = kNone, kmin = INT_MAX;
   if (!__all_sync(0xffffffffu, chunk_keys(ch, key, cmax, kmin)))

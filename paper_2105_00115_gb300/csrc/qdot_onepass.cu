@@ -62,7 +62,9 @@ struct OpHeader {
   int status;
   int erun;            // running lower bound of e_max shared by the streaming warps (biased)
   long long zeros;
-  unsigned done;       // gather CTAs that have written their partial (zeroed by k_op_select)
+  unsigned done;       // CTAs that have written their partial (zeroed by k_op_select)
+  unsigned pad;
+  unsigned long long nredo;  // item records: items the gather listed for k_items_redo (zeroed by k_op_select)
 };
 struct OpPart {
   i128 sum;
@@ -330,6 +332,7 @@ __global__ void __launch_bounds__(1024) k_op_select(const WarpStats* __restrict_
     hdr->status = status;
     hdr->zeros = z;
     hdr->done = 0u;
+    hdr->nredo = 0ull;
   }
   __syncthreads();
   const int e_max = sel->e_max, f = s_f;
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(1024) k_op_select(const WarpStats* __restrict_
 // the result, rounding once.
 __device__ __noinline__ void finish_gather(i128 acc, unsigned long long (&c)[5], OpPart* __restrict__ parts,
                               OpHeader* __restrict__ hdr, qdot_selection* __restrict__ sel,
-                              qdot_result* __restrict__ out) {
+                              qdot_result* __restrict__ out, int slot0 = 0, bool final = true) {
   __shared__ i128 s_sum[8];
   __shared__ unsigned long long s_cnt[8][5];
   __shared__ bool s_last;
@@ -370,15 +373,19 @@ __device__ __noinline__ void finish_gather(i128 acc, unsigned long long (&c)[5],
       for (int k = 0; k < 4; ++k) p.cnt[k] += s_cnt[i][k];
       p.repairs += s_cnt[i][4];
     }
-    parts[blockIdx.x] = p;
-    __threadfence();  // the partial is visible before the arrival is counted
-    s_last = atomicAdd(&hdr->done, 1u) == gridDim.x - 1;
+    parts[slot0 + blockIdx.x] = p;
+    if (final) {
+      __threadfence();  // the partial is visible before the arrival is counted
+      s_last = atomicAdd(&hdr->done, 1u) == gridDim.x - 1;
+    }
   }
+  if (!final) return;  // a later kernel of the same stream adds the partials
   __syncthreads();
   if (!s_last) return;
-  // last CTA: the exact sum of the partials, in CTA order, then one rounding
+  // last CTA: the exact sum of the partials (slots 0 .. slot0 + grid - 1, in
+  // order), then one rounding
   __threadfence();
-  const int np = gridDim.x;
+  const int np = slot0 + (int)gridDim.x;
   acc = 0;
   #pragma unroll
   for (int k = 0; k < 5; ++k) c[k] = 0;
@@ -702,12 +709,11 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
 
 
 // Gather of item records: an item whose bound e_lo was e_max, and f_spec f, adds
-// its record; any other item is recomputed with the final classes.  The CTA
-// takes kGatherPer x 256 items per round, kGatherPer per thread with
-// independent loads, and its warps recompute the rejected ones of each round
-// together.  Items are dealt to the CTAs in turn (item i to CTA i mod grid):
-// the rejected items are mostly every warp's first few, at the start of the
-// vectors, and this spreads them evenly.
+// its record; every other item goes to a list that k_items_redo sums again
+// with the final classes.  The CTA takes kGatherPer x 256 records per round,
+// kGatherPer per thread with independent loads; the rejected ones of a round
+// are appended to the list together (one atomic per CTA and round).  The
+// CTA's partial goes to parts[blockIdx.x]; k_items_redo adds the partials.
 constexpr int kGatherPer = 4;
 
 template <int LOG2B>
@@ -715,22 +721,17 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
                                                      const unsigned long long* __restrict__ imeta, long long nitems,
                                                      int f_spec, qdot_selection* __restrict__ sel,
                                                      OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
-                                                     const double* __restrict__ x, const double* __restrict__ y,
-                                                     long long n, qdot_result* __restrict__ out,
-                                                     qdot_trace_unit* __restrict__ trace, uint8_t* __restrict__ tcls) {
-  __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
+                                                     long long* __restrict__ redo,
+                                                     qdot_trace_unit* __restrict__ trace) {
   __shared__ long long s_qitem[256 * kGatherPer];
   __shared__ int s_nqueue;
-  for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
+  __shared__ unsigned long long s_base;
   if (threadIdx.x == 0) s_nqueue = 0;
   __syncthreads();
   const int lsb = hdr->lsb;
   const bool ok = hdr->status == QDOT_OK;
   const unsigned anchor = (unsigned)(sel->e_max + 2046);  // the bound an exact item recorded
   const bool f_exact = sel->f == f_spec;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  i128 acc = 0;
   unsigned long long acc_lo = 0;
   long long acc_hi = 0;
   unsigned long long c[5] = {0, 0, 0, 0, 0};
@@ -770,20 +771,61 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
     }
     __syncthreads();
     const int nq = s_nqueue;
-    for (int qi = w; qi < nq; qi += (int)(blockDim.x >> 5)) {
-      int u;
-      const long long vv = recompute_item_fast<LOG2B>(x, y, n, s_qitem[qi], s_lut, lane, &u, c, tcls);
-      if (lane == 0 && u != kNone) acc += candidate_to_fixed(vv, kSingle, u, 8, lsb);  // grid 2^(u - 52)
-      if (lane == 0 && trace)
-        trace[s_qitem[qi]] = qdot_trace_unit{u != kNone ? vv : 0ll, u != kNone ? u - 52 : 0, 255,
-                                             (uint8_t)QDOT_TRACE_ITEM_RECOMPUTED, 0};
-    }
+    if (threadIdx.x == 0 && nq) s_base = atomicAdd(&hdr->nredo, (unsigned long long)nq);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nq; t += blockDim.x) redo[s_base + t] = s_qitem[t];
     __syncthreads();
     if (threadIdx.x == 0) s_nqueue = 0;
     __syncthreads();
   }
-  acc += (i128)(((unsigned __int128)(unsigned long long)acc_hi << 64) | acc_lo);
-  finish_gather(acc, c, parts, hdr, sel, out);
+  const i128 acc = (i128)(((unsigned __int128)(unsigned long long)acc_hi << 64) | acc_lo);
+  finish_gather(acc, c, parts, hdr, sel, nullptr, 0, false);
+}
+
+// The items the gather listed, summed again with the final classes (the
+// selection's table) in the streaming kernel's arithmetic
+// (recompute_loaded_item), at streaming speed: the warps take the list in
+// turn and load each item one ahead in registers.  The gather's partials sit
+// in parts[0 .. gather_grid - 1], this kernel's after them; the last CTA to
+// finish adds them all in order and rounds once.
+template <int LOG2B>
+__global__ void __launch_bounds__(256, 2) k_items_redo(const double* __restrict__ x, const double* __restrict__ y,
+                                                long long n, const long long* __restrict__ redo,
+                                                qdot_selection* __restrict__ sel, OpHeader* __restrict__ hdr,
+                                                OpPart* __restrict__ parts, int gather_grid,
+                                                qdot_result* __restrict__ out, qdot_trace_unit* __restrict__ trace,
+                                                uint8_t* __restrict__ tcls) {
+  constexpr int LB = LOG2B ? LOG2B : 8;
+  __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
+  for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
+  __syncthreads();
+  const int lsb = hdr->lsb;
+  const long long m = hdr->status == QDOT_OK ? (long long)hdr->nredo : 0ll;
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  i128 acc = 0;
+  unsigned long long c[5] = {0, 0, 0, 0, 0};
+  Chunk cur, nxt;
+  long long j = gwarp;
+  long long it = j < m ? redo[j] : 0;
+  if (j < m) load_item<LB>(x, y, n, it, lane, cur);
+  for (; j < m; j += nwarps) {
+    const long long jn = j + nwarps;
+    const long long itn = jn < m ? redo[jn] : 0;
+    if (jn < m) load_item<LB>(x, y, n, itn, lane, nxt);  // in flight while this item is summed
+    int u;
+    const long long v = recompute_loaded_item<LOG2B>(x, y, n, it, cur, s_lut, lane, &u, c, tcls);
+    if (lane == 0 && u != kNone) acc += candidate_to_fixed(v, kSingle, u, 8, lsb);  // grid 2^(u - 52)
+    if (lane == 0 && trace)
+      trace[it] = qdot_trace_unit{u != kNone ? v : 0ll, u != kNone ? u - 52 : 0, 255,
+                                  (uint8_t)QDOT_TRACE_ITEM_RECOMPUTED, 0};
+    cur = nxt;
+    it = itn;
+  }
+  c[4] = 0;  // the gather counted the listed items
+  finish_gather(acc, c, parts, hdr, sel, out, gather_grid, true);
 }
 
 // The largest k with N * 2^k <= eps (host side; only steers which candidates
@@ -864,9 +906,13 @@ cudaError_t launch_items(const double* x, const double* y, int64_t n, const qdot
                                                                  imeta, tr.cls);
   if (ev1) cudaEventRecord(ev1, st);
   k_op_select<<<1, 1024, 0, st>>>(wst, pl.grid * kOpWarps, n, *p, sel, hdr);
-  const int gather_grid = 2 * (device_info().sms > 0 ? device_info().sms : 152);  // 2 CTAs per SM
-  k_op_gather_items<LOG2B><<<gather_grid, 256, 0, st>>>(isum, imeta, nitems, f_spec, sel, hdr, parts, x, y, n,
-                                                         out, tr.units, tr.cls);
+  const int sms = device_info().sms > 0 ? device_info().sms : 152;
+  const int gather_grid = 2 * sms, redo_grid = 2 * sms;  // 2 CTAs per SM each; 4 x sms partial slots
+  auto* redo = reinterpret_cast<long long*>(ws + pl.off_slot1);
+  k_op_gather_items<LOG2B><<<gather_grid, 256, 0, st>>>(isum, imeta, nitems, f_spec, sel, hdr, parts, redo,
+                                                         tr.units);
+  k_items_redo<LOG2B><<<redo_grid, 256, 0, st>>>(x, y, n, redo, sel, hdr, parts, gather_grid, out, tr.units,
+                                                  tr.cls);
   return cudaGetLastError();
 }
 
@@ -876,7 +922,8 @@ bool one_pass_supported(int64_t n, const qdot_params* p, bool aligned16) {
   return aligned16 && n > 0 && (p->block == 1 || (p->block >= 32 && p->block <= 256));
 }
 
-int one_pass_launches(int64_t, const qdot_params*) { return 3; }  // stream, select, gather
+// stream, select, gather (+ the item records' redo)
+int one_pass_launches(int64_t n, const qdot_params* p) { return plan_one_pass(n, p).items ? 4 : 3; }
 
 const char* one_pass_stream_kernel(int64_t n, const qdot_params* p) {
   return plan_one_pass(n, p).items ? "k_onepass_items" : "k_onepass";
@@ -905,6 +952,8 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
     off = align_up(off + sizeof(long long) * (size_t)nitems, 256);
     pl.off_meta = off;
     off = align_up(off + sizeof(unsigned long long) * (size_t)nitems, 256);
+    pl.off_slot1 = off;  // the list of items the gather rejects (k_items_redo)
+    off = align_up(off + sizeof(long long) * (size_t)nitems, 256);
     pl.total = off;
     return pl;
   }
