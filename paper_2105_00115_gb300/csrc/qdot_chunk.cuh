@@ -708,6 +708,23 @@ __device__ __forceinline__ long long recompute_chain_lane(const double* __restri
   return __double2ll_rz(a * chain_scale<LOG2B>(cls));
 }
 
+// recompute_chain_lane() on components the warp has already loaded in the
+// streaming layout (`ch`, from load_item): the same chain, the same value.
+template <int LOG2B>
+__device__ __forceinline__ long long chain_lane_loaded(const Chunk& ch, int u, int cls) {
+  double a = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (!((ch.vmask >> j) & 1u)) continue;
+    const uint64_t xb = ch.x[j], yb = ch.y[j];
+    if (is_zero(xb) || is_zero(yb)) continue;
+    uint64_t xo, yo;
+    chain_operands(xb, yb, u - (exponent_of(xb) + exponent_of(yb)), xo, yo);
+    a = chain_step(xo, yo, cls, a);
+  }
+  return __double2ll_rz(a * chain_scale<LOG2B>(cls));
+}
+
 // The candidate of class cls of block blk by one thread (every lane's chain
 // in turn) ...
 template <int LOG2B>

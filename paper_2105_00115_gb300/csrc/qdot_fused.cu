@@ -238,16 +238,32 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm)
   // Theorem 5: every score is at least m_single, so every block is DOUBLE
   const bool all_double = (long long)e_max - s_emin <= -(long long)f - ms;
   if (!s_bad) {
+    // HALF and SINGLE blocks are summed again from x and y (in L2 at these
+    // sizes): a warp loads the next item that has such a block while it sums
+    // the current one, so the L2 round trips overlap
+    auto block_class = [&](int kk) {
+      const FusedBlock b = s_blk[w][kk][g];
+      return b.key == (int)kEmptyKey ? kZero
+                                     : (all_double ? kDouble : precision_of((long long)b.key - e_max - f + 1, mh, ms));
+    };
+    auto needs_chain = [&](int kk) {  // warp-uniform
+      const int c = block_class(kk);
+      return __any_sync(0xffffffffu, c == kHalf || c == kSingle);
+    };
+    bool need_cur = k > 0 && !all_double && needs_chain(0);
+    if (need_cur) load_item<LOG2B>(x, y, n, gwarp, lane, cur);
     for (int kk = 0; kk < k; ++kk) {  // k is the same in every lane of the warp
+      const bool need_nxt = kk + 1 < k && !all_double && needs_chain(kk + 1);
+      if (need_nxt) load_item<LOG2B>(x, y, n, gwarp + (kk + 1) * nwarps, lane, nxt);
       const FusedBlock b = s_blk[w][kk][g];
       const long long blk = (gwarp + kk * nwarps) * BPI + g;
       const bool empty = b.key == (int)kEmptyKey;
-      const int cls = empty ? kZero : (all_double ? kDouble : precision_of((long long)b.key - e_max - f + 1, mh, ms));
+      const int cls = block_class(kk);
       const int u = empty ? 0 : b.key - ceil_log2_u32(b.m);
-      // HALF and SINGLE blocks: every lane of the block sums its chain again
-      // (no shuffle inside the branch), then the block's lanes add up
+      // every lane of a HALF or SINGLE block sums its chain (no shuffle
+      // inside the branch), then the block's lanes add up
       long long lv = 0;
-      if (cls == kHalf || cls == kSingle) lv = recompute_chain_lane<LOG2B>(x, y, n, blk, u, cls, sub);
+      if (need_cur && (cls == kHalf || cls == kSingle)) lv = chain_lane_loaded<LOG2B>(cur, u, cls);
       if (!all_double) lv = group_sum<L>(lv);
       if (sub == 0 && !empty) {
 #pragma unroll
@@ -260,6 +276,8 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedCtasPerSm)
       }
       if (sub == 0 && empty && trace && blk < nblocks)
         trace[blk] = qdot_trace_unit{0ll, 0, (uint8_t)kZero, (uint8_t)QDOT_TRACE_NONE, 0};
+      cur = nxt;
+      need_cur = need_nxt;
     }
   }
   acc = warp_sum_i128(acc);
