@@ -349,7 +349,10 @@ enum {
   QDOT_TRACE_RECOMPUTED = 4,       /* the candidate was not kept; recomputed from x, y */
   QDOT_TRACE_FUSED = 5,            /* the fused kernel's candidate of the block's class */
   QDOT_TRACE_ITEM = 6,             /* the item's record, accepted */
-  QDOT_TRACE_ITEM_RECOMPUTED = 7   /* the item recomputed with the final classes */
+  QDOT_TRACE_ITEM_RECOMPUTED = 7,  /* the item recomputed with the final classes */
+  QDOT_TRACE_ITEM_FIXED = 8        /* blocks of 32 .. 256 on item records: the record, with the
+                                      blocks whose class the final selection changed summed
+                                      again from x, y and swapped in */
 };
 
 /* Number of qdot_trace_unit records qdot_trace() writes for these arguments,

@@ -39,7 +39,7 @@ class TraceUnit(ctypes.Structure):
 
 # qdot_trace_unit sources (include/qdot.h)
 TRACE_SOURCES = {0: "none", 1: "slot0", 2: "slot1", 3: "slot3", 4: "recomputed", 5: "fused", 6: "item",
-                 7: "item_recomputed"}
+                 7: "item_recomputed", 8: "item_fixed"}
 
 
 class Csr(ctypes.Structure):

@@ -67,6 +67,7 @@ struct OnePassPlan {
   long long unit_blocks = 0;
   bool items = false;  // item records (one per 256 components) instead of block records
   size_t off_sel = 0, off_hdr = 0, off_rec = 0, off_misc = 0, off_slot1 = 0, off_meta = 0, off_slot3 = 0;
+  size_t off_rec2 = 0;
   size_t rec_bytes = 0;
   size_t total = 0;
 };

@@ -65,6 +65,7 @@ struct OpHeader {
   unsigned done;       // CTAs that have written their partial (zeroed by k_op_select)
   unsigned pad;
   unsigned long long nredo;  // item records: items the gather listed for k_items_redo (zeroed by k_op_select)
+  unsigned long long nfix;   // item records of blocks: blocks the gather listed for k_items_redo (zeroed too)
 };
 struct OpPart {
   i128 sum;
@@ -333,6 +334,7 @@ __global__ void __launch_bounds__(1024) k_op_select(const WarpStats* __restrict_
     hdr->zeros = z;
     hdr->done = 0u;
     hdr->nredo = 0ull;
+    hdr->nfix = 0ull;
   }
   __syncthreads();
   const int e_max = sel->e_max, f = s_f;
@@ -573,6 +575,7 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
                                                                  WarpStats* __restrict__ wstats,
                                                                  long long* __restrict__ isum,
                                                                  unsigned long long* __restrict__ imeta,
+                                                                 unsigned long long* __restrict__ iblk,
                                                                  uint8_t* __restrict__ tcls) {
   constexpr int LB = LOG2B ? LOG2B : 8;  // the item layout (blocks of one: that of 256)
   constexpr int L = Map<LB>::L;
@@ -633,7 +636,16 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
           for (int j = 0; j < 8; ++j) tcls[it * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls[j];
         }
       } else {
-        const int sg = LB + group_max<L>(cmax) - a;  // the block's score (M_b = B)
+        const int ub = group_max<L>(cmax);  // the block's largest key (biased)
+        {  // one byte per block: u - u_b, saturated at 255 (the gather's per-block check)
+          const unsigned du = (unsigned)min(u - ub, 255);
+          unsigned long long word = 0;
+#pragma unroll
+          for (int g = 0; g < Map<LB>::BPI; ++g)
+            word |= (unsigned long long)__shfl_sync(0xffffffffu, du, g * L) << (8 * g);
+          if (lane == 0) iblk[it] = word;
+        }
+        const int sg = LB + ub - a;  // the block's score (M_b = B)
         const int cls = sg < 0 ? kPerf : (sg < mh ? kHalf : (sg < ms ? kSingle : kDouble));
         const unsigned prim = cls == kPerf ? 0u : 1u << cls;
         double aH2 = 0.0, aS2 = 0.0;
@@ -721,7 +733,8 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
                                                      const unsigned long long* __restrict__ imeta, long long nitems,
                                                      int f_spec, qdot_selection* __restrict__ sel,
                                                      OpHeader* __restrict__ hdr, OpPart* __restrict__ parts,
-                                                     long long* __restrict__ redo,
+                                                     const unsigned long long* __restrict__ iblk,
+                                                     long long* __restrict__ redo, long long* __restrict__ fix,
                                                      qdot_trace_unit* __restrict__ trace) {
   __shared__ long long s_qitem[256 * kGatherPer];
   __shared__ int s_nqueue;
@@ -732,25 +745,59 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
   const bool ok = hdr->status == QDOT_OK;
   const unsigned anchor = (unsigned)(sel->e_max + 2046);  // the bound an exact item recorded
   const bool f_exact = sel->f == f_spec;
+  // blocks: score = s_b - a with the anchor a = e_lo + f - 1 (biased keys)
+  const int a_true = sel->e_max + 2046 + sel->f - 1;
+  const int mh = sel->m_half, ms = sel->m_single;
   unsigned long long acc_lo = 0;
   long long acc_hi = 0;
   unsigned long long c[5] = {0, 0, 0, 0, 0};
   const long long G = gridDim.x;
   const long long T = blockDim.x;
   for (long long q0 = 0; ok && q0 * G + blockIdx.x < nitems; q0 += T * kGatherPer) {
-    unsigned long long m[kGatherPer];
+    unsigned long long m[kGatherPer], bws[kGatherPer];
     long long v[kGatherPer];
+    long long fx[LOG2B ? kGatherPer * Map<LOG2B ? LOG2B : 8>::BPI : 1];  // this thread's block entries
+    int nfx = 0;
 #pragma unroll
     for (int k = 0; k < kGatherPer; ++k) {  // independent loads first
       const long long i = (q0 + threadIdx.x + k * T) * G + blockIdx.x;
       m[k] = i < nitems ? imeta[i] : 0ull;
       v[k] = i < nitems ? isum[i] : 0ll;
+      bws[k] = (LOG2B > 0 && i < nitems) ? iblk[i] : 0ull;
     }
 #pragma unroll
     for (int k = 0; k < kGatherPer; ++k) {
       const long long i = (q0 + threadIdx.x + k * T) * G + blockIdx.x;
       if (i >= nitems) continue;
-      if (f_exact && !(m[k] & kItemRecompute) && (unsigned)((m[k] >> 12) & 0xFFFu) == anchor) {
+      bool accept = f_exact && !(m[k] & kItemRecompute) && (unsigned)((m[k] >> 12) & 0xFFFu) == anchor;
+      unsigned flip = 0;
+      if (LOG2B > 0 && !accept && !(m[k] & kItemRecompute)) {
+        // blocks: the anchor was stale, but only blocks whose class the final
+        // anchor changes matter (a block 255 or more keys below the item's
+        // largest is recomputed with the whole item)
+        const int a_used = (int)((m[k] >> 12) & 0xFFFu) + f_spec - 1;
+        const int ui = (int)(m[k] & 0xFFFu);
+        const unsigned long long bw = bws[k];
+        bool far = false;
+#pragma unroll
+        for (int g = 0; g < Map<LOG2B ? LOG2B : 8>::BPI; ++g) {
+          const int du = (int)((bw >> (8 * g)) & 0xFFu);
+          far |= du == 255;
+          const int sb = LOG2B + ui - du;
+          flip |= precision_of(sb - a_used, mh, ms) != precision_of(sb - a_true, mh, ms) ? (1u << g) : 0u;
+        }
+        // the blocks' corrections are added apart from the record, which is exact
+        // only while the item's grid 2^(u - 52) is not finer than the sum's
+        const bool coarse = ui - 2046 - 52 >= lsb;
+        if (far || !coarse) flip = 0;
+        accept = !far && coarse;  // with flip != 0: the record now, its changed blocks in k_items_redo
+      }
+      if (flip) {  // entries: (1 << 62) | u << 50 | e_lo << 38 | block index
+        const unsigned long long hi = (1ull << 62) | ((m[k] & 0xFFFull) << 50) | (((m[k] >> 12) & 0xFFFull) << 38);
+        const long long b0 = i * Map<LOG2B ? LOG2B : 8>::BPI;
+        for (unsigned f2 = flip; f2; f2 &= f2 - 1) fx[nfx++] = (long long)(hi | (unsigned long long)(b0 + __ffs(f2) - 1));
+      }
+      if (accept) {
         const unsigned nh = (unsigned)(m[k] >> 24) & 0x1FFu, ns = (unsigned)(m[k] >> 33) & 0x1FFu,
                        nd = (unsigned)(m[k] >> 42) & 0x1FFu;
         c[kHalf] += nh;
@@ -763,11 +810,26 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
         const unsigned long long lo = (unsigned long long)wv << sl;
         acc_lo += lo;
         acc_hi += ((wv >> 1) >> (63 - sl)) + (acc_lo < lo ? 1 : 0);
-        if (trace) trace[i] = qdot_trace_unit{v[k], (int)(m[k] & 0xFFFu) - 2046 - 52, 255, (uint8_t)QDOT_TRACE_ITEM, 0};
+        if (trace)
+          trace[i] = qdot_trace_unit{v[k], (int)(m[k] & 0xFFFu) - 2046 - 52, 255,
+                                     (uint8_t)(flip ? QDOT_TRACE_ITEM_FIXED : QDOT_TRACE_ITEM), 0};
       } else {
-        ++c[4];
-        s_qitem[atomicAdd(&s_nqueue, 1)] = i;  // at most kGatherPer per thread and round
+        ++c[4];  // at most kGatherPer per thread and round
+        s_qitem[atomicAdd(&s_nqueue, 1)] = i;
       }
+    }
+    if (LOG2B > 0) {  // block entries: one atomic per warp
+      const int lane = threadIdx.x & 31;
+      int incl = nfx;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      unsigned long long wbase = 0;
+      if (lane == 31 && incl) wbase = atomicAdd(&hdr->nfix, (unsigned long long)incl);
+      wbase = __shfl_sync(0xffffffffu, wbase, 31);
+      for (int t = 0; t < nfx; ++t) fix[wbase + incl - nfx + t] = fx[t];
     }
     __syncthreads();
     const int nq = s_nqueue;
@@ -782,31 +844,103 @@ __global__ void __launch_bounds__(256, 2) k_op_gather_items(const long long* __r
   finish_gather(acc, c, parts, hdr, sel, nullptr, 0, false);
 }
 
-// The items the gather listed, summed again with the final classes (the
-// selection's table) in the streaming kernel's arithmetic
-// (recompute_loaded_item), at streaming speed: the warps take the list in
-// turn and load each item one ahead in registers.  The gather's partials sit
-// in parts[0 .. gather_grid - 1], this kernel's after them; the last CTA to
-// finish adds them all in order and rounds once.
+// The work the gather listed, summed again at streaming speed.
+// 1. Blocks of 32 .. 256 whose class changed under the final anchor in an item
+//    whose record the gather kept (its sum was formed with the stale anchor
+//    a_used = e_lo + f_spec - 1; the final a_true is larger, so a block's class
+//    can only drop): a warp takes 256 / B such blocks at once, B / 8 lanes per
+//    block as in the streaming layout.  Each lane forms its chain with the
+//    class the streaming kernel used and with the final class, exactly as the
+//    streaming kernel forms a chain, and the difference of the truncated lane
+//    values (on the item's grid 2^(u - 52), no finer than the sum's, which the
+//    gather checked) is added to the sum.
+// 2. Items the gather rejected: each summed with the final classes (the
+//    selection's table) in the streaming kernel's arithmetic
+//    (recompute_loaded_item); the warps take the list in turn and load each
+//    item one ahead in registers.
+// The gather's partials sit in parts[0 .. gather_grid - 1], this kernel's
+// after them; the last CTA to finish adds them all in order and rounds once.
 template <int LOG2B>
 __global__ void __launch_bounds__(256, 2) k_items_redo(const double* __restrict__ x, const double* __restrict__ y,
                                                 long long n, const long long* __restrict__ redo,
+                                                const long long* __restrict__ fix, int f_spec,
                                                 qdot_selection* __restrict__ sel, OpHeader* __restrict__ hdr,
                                                 OpPart* __restrict__ parts, int gather_grid,
                                                 qdot_result* __restrict__ out, qdot_trace_unit* __restrict__ trace,
                                                 uint8_t* __restrict__ tcls) {
   constexpr int LB = LOG2B ? LOG2B : 8;
+  constexpr int L = Map<LB>::L, BPI = Map<LB>::BPI, B = 1 << LB;
   __shared__ __align__(16) uint8_t s_lut[kKeyCount];  // filled as 32-bit words
   for (int i = threadIdx.x; i < kKeyCount / 4; i += blockDim.x)
     reinterpret_cast<uint32_t*>(s_lut)[i] = reinterpret_cast<const uint32_t*>(sel->cls)[i];
   __syncthreads();
   const int lsb = hdr->lsb;
-  const long long m = hdr->status == QDOT_OK ? (long long)hdr->nredo : 0ll;
+  const bool ok = hdr->status == QDOT_OK;
+  const long long m = ok ? (long long)hdr->nredo : 0ll;
   const int lane = threadIdx.x & 31;
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   i128 acc = 0;
   unsigned long long c[5] = {0, 0, 0, 0, 0};
+  if (LOG2B > 0) {  // 1. changed blocks
+    const long long nf = ok ? (long long)hdr->nfix : 0ll;
+    const int a_true = sel->e_max + 2046 + sel->f - 1;
+    const int mh = sel->m_half, ms = sel->m_single;
+    const int g = lane / L, sub = lane % L;
+    for (long long b0 = gwarp * BPI; b0 < nf; b0 += nwarps * BPI) {  // warp-uniform
+      const long long idx = b0 + g;
+      const bool have = idx < nf;
+      const unsigned long long E = have ? (unsigned long long)fix[idx] : 0ull;
+      const long long blk = (long long)(E & ((1ull << 38) - 1));
+      const int u = (int)((E >> 50) & 0xFFFu), elo = (int)((E >> 38) & 0xFFFu);
+      const long long item = blk / BPI;
+      const int gi = (int)(blk % BPI);
+      Chunk ch;
+      ch.vmask = 0xFFu;
+      if (have) {  // the block lies in a plain item, inside the vectors
+        const long long base = item * kItem + item_offset<LB>(gi * L + sub, 0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const double2 av = __ldcs(reinterpret_cast<const double2*>(x + base + 2 * L * j));
+          const double2 bv = __ldcs(reinterpret_cast<const double2*>(y + base + 2 * L * j));
+          ch.x[2 * j] = (uint64_t)__double_as_longlong(av.x);
+          ch.x[2 * j + 1] = (uint64_t)__double_as_longlong(av.y);
+          ch.y[2 * j] = (uint64_t)__double_as_longlong(bv.x);
+          ch.y[2 * j + 1] = (uint64_t)__double_as_longlong(bv.y);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ch.x[j] = ch.y[j] = 0ull;
+      }
+      int key[8];
+      int cmax = kNone, kmin = INT_MAX;
+      chunk_keys(ch, key, cmax, kmin);
+      const int ub = group_max<L>(cmax);  // every lane joins its block's shuffles
+      const int c_old = precision_of((long long)LB + ub - (elo + f_spec - 1), mh, ms);
+      const int c_new = precision_of((long long)LB + ub - a_true, mh, ms);
+      long long d = 0;
+      if (have) {
+        const unsigned p_old = c_old == kPerf ? 0u : 1u << c_old, p_new = c_new == kPerf ? 0u : 1u << c_new;
+        double h = 0.0, sg = 0.0, a0 = 0.0, a1 = 0.0;
+        acc_lane<LB, 3, 0u>(ch, key, u, p_old, h, sg, a0);
+        acc_lane<LB, 3, 0u>(ch, key, u, p_new, h, sg, a1);
+        d = (p_new ? __double2ll_rz(a1 * 4503599627370496.0) : 0ll) -
+            (p_old ? __double2ll_rz(a0 * 4503599627370496.0) : 0ll);  // grid 2^(u - 52)
+        if (tcls) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tcls[item * kItem + item_offset<LB>(gi * L + sub, j)] = (uint8_t)c_new;
+        }
+      }
+      d = group_sum<L>(d);
+      if (have && sub == 0) {
+        acc += candidate_to_fixed(d, kSingle, u - 2046, 8, lsb);  // exact: the gather checked the grid
+        c[c_old] -= (unsigned long long)B;
+        c[c_new] += (unsigned long long)B;
+        if (trace) atomicAdd(reinterpret_cast<unsigned long long*>(&trace[item].value), (unsigned long long)d);
+      }
+    }
+  }
+  // 2. rejected items
   Chunk cur, nxt;
   long long j = gwarp;
   long long it = j < m ? redo[j] : 0;
@@ -902,17 +1036,19 @@ cudaError_t launch_items(const double* x, const double* y, int64_t n, const qdot
     if (e != cudaSuccess) return e;
     smem_set = true;
   }
+  auto* iblk = LOG2B ? reinterpret_cast<unsigned long long*>(ws + pl.off_slot3) : nullptr;
   k_onepass_items<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, isum,
-                                                                 imeta, tr.cls);
+                                                                 imeta, iblk, tr.cls);
   if (ev1) cudaEventRecord(ev1, st);
   k_op_select<<<1, 1024, 0, st>>>(wst, pl.grid * kOpWarps, n, *p, sel, hdr);
   const int sms = device_info().sms > 0 ? device_info().sms : 152;
   const int gather_grid = 2 * sms, redo_grid = 2 * sms;  // 2 CTAs per SM each; 4 x sms partial slots
   auto* redo = reinterpret_cast<long long*>(ws + pl.off_slot1);
-  k_op_gather_items<LOG2B><<<gather_grid, 256, 0, st>>>(isum, imeta, nitems, f_spec, sel, hdr, parts, redo,
-                                                         tr.units);
-  k_items_redo<LOG2B><<<redo_grid, 256, 0, st>>>(x, y, n, redo, sel, hdr, parts, gather_grid, out, tr.units,
-                                                  tr.cls);
+  auto* fix = LOG2B ? reinterpret_cast<long long*>(ws + pl.off_rec2) : nullptr;
+  k_op_gather_items<LOG2B><<<gather_grid, 256, 0, st>>>(isum, imeta, nitems, f_spec, sel, hdr, parts, iblk, redo,
+                                                         fix, tr.units);
+  k_items_redo<LOG2B><<<redo_grid, 256, 0, st>>>(x, y, n, redo, fix, f_spec, sel, hdr, parts, gather_grid, out,
+                                                  tr.units, tr.cls);
   return cudaGetLastError();
 }
 
@@ -954,6 +1090,12 @@ OnePassPlan plan_one_pass(int64_t n, const qdot_params* p) {
     off = align_up(off + sizeof(unsigned long long) * (size_t)nitems, 256);
     pl.off_slot1 = off;  // the list of items the gather rejects (k_items_redo)
     off = align_up(off + sizeof(long long) * (size_t)nitems, 256);
+    if (p->block >= 32) {
+      pl.off_slot3 = off;  // per item: how far each block's largest key lies below the item's
+      off = align_up(off + sizeof(unsigned long long) * (size_t)nitems, 256);
+      pl.off_rec2 = off;  // the list of blocks whose class the final selection changed
+      off = align_up(off + sizeof(long long) * (size_t)nblocks, 256);
+    }
     pl.total = off;
     return pl;
   }

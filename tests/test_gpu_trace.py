@@ -29,7 +29,8 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-13
-SRC = {"none": 0, "slot0": 1, "slot1": 2, "slot3": 3, "recomputed": 4, "fused": 5, "item": 6, "item_recomputed": 7}
+SRC = {"none": 0, "slot0": 1, "slot1": 2, "slot3": 3, "recomputed": 4, "fused": 5, "item": 6, "item_recomputed": 7,
+       "item_fixed": 8}
 
 
 @pytest.fixture(scope="module")
@@ -188,21 +189,26 @@ def test_trace_one_pass_items_blocks_of_32(q, orc):
         xd, yd = _dev(x), _dev(y)
         for eps in (1e-15, 1e-8, 1e-1):
             _, units = check_trace(q, orc, x, y, eps, 32, expect_kernel="k_onepass_items", xd=xd, yd=yd)
-            assert set(np.unique(units["source"]).tolist()) <= {SRC["item"], SRC["item_recomputed"]}
+            assert set(np.unique(units["source"]).tolist()) <= {SRC["item"], SRC["item_recomputed"],
+                                                                 SRC["item_fixed"]}
     x, y = workloads.pair("c", n, 601)
     sparse = x.copy()
     sparse[rng.random(n) < 0.01] = 0.0
     ramp = x * np.exp2(np.linspace(0.0, 40.0, n))
     for xx in (sparse, ramp):
         _, units = check_trace(q, orc, xx, y, 1e-8, 32, expect_kernel="k_onepass_items")
-        assert np.count_nonzero(units["source"] == SRC["item_recomputed"]) > 0
+        assert np.count_nonzero(np.isin(units["source"], (SRC["item_recomputed"], SRC["item_fixed"]))) > 0
 
 
 def test_trace_items_late_maximum(q, orc):
     """Blocks of 32 and of one on item records when the largest product sits in
     the last item: every earlier item was summed with a bound of e_max below
-    the final one and is summed again with the final classes; every item's
-    value and the class map must still be the oracle's."""
+    the final one.  Blocks of one: those items are summed again.  Blocks of
+    32: an item whose blocks all keep their class is taken as recorded; in the
+    others only the changed blocks are summed again and swapped in
+    (QDOT_TRACE_ITEM_FIXED), unless the item's grid is finer than the final
+    sum's, where the item is summed again whole.  Every item's value and the class map must still be the
+    oracle's."""
     n = (1 << 25) + 256 * 7
     x, y = workloads.pair("b", n, 602)
     for spike in (2.0**3, 2.0**10):  # the last item's product lies 6 or 20 binades above the rest
@@ -211,8 +217,18 @@ def test_trace_items_late_maximum(q, orc):
         yy[-3] = np.abs(y).max() * spike
         xd, yd = _dev(xx), _dev(yy)
         for block, eps in ((32, 1e-15), (32, 1e-8), (32, 1e-1), (1, 1e-8)):
-            _, units = check_trace(q, orc, xx, yy, eps, block, expect_kernel="k_onepass_items", xd=xd, yd=yd)
-            assert np.count_nonzero(units["source"] == SRC["item_recomputed"]) > units.size // 2
+            r, units = check_trace(q, orc, xx, yy, eps, block, expect_kernel="k_onepass_items", xd=xd, yd=yd)
+            src = units["source"]
+            if block == 1:
+                assert np.count_nonzero(src == SRC["item_recomputed"]) > src.size // 2
+            else:
+                assert np.count_nonzero(src == SRC["item_fixed"]) > 0
+                # only items whose grid 2^(u - 52) is finer than the sum's 2^(e_max - L) are summed again whole
+                keys = (np.frexp(xx)[1] - 1) + (np.frexp(yy)[1] - 1)
+                u = keys.reshape(-1, 256).max(axis=1)
+                L = min(104, 124 - int(np.ceil(np.log2(n))))
+                fine = np.count_nonzero(u - 52 < r.e_max - L)
+                assert np.count_nonzero(src == SRC["item_recomputed"]) <= fine + 3 * 3648  # + every warp's first items
 
 
 def test_trace_repeatable_bit_for_bit(q, orc):
