@@ -563,6 +563,39 @@ __global__ void __launch_bounds__(256, 4) k_op_gather(const long long* __restric
 constexpr unsigned long long kItemRecompute = 1ull << 63;
 
 
+// The largest key (biased) of the items the streaming warps take first (the
+// first kSeedRounds items of every warp, in the streaming kernel's order)
+// into the shared bound erun before the stream starts.  Without it a warp
+// sums its first items with its own bound alone, which is far below e_max;
+// with it those items start from the bound the warps would otherwise learn
+// only after a few exchanges.  The items stay in L2 for the stream (about
+// 0.7% of the vectors at 2^28).  Any value it writes is a key of the vectors,
+// so a lower bound of e_max.
+constexpr int kSeedRounds = 2;
+
+__global__ void __launch_bounds__(kOpThreads) k_seed_bound(const double* __restrict__ x,
+                                                           const double* __restrict__ y, long long n,
+                                                           long long nwarps_stream, int* __restrict__ erun) {
+  const int lane = threadIdx.x & 31;
+  const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nitems = (n + kItem - 1) / kItem;
+  int wmax = kNone;
+  for (int r = 0; r < kSeedRounds; ++r) {
+    const long long item = gwarp + r * nwarps_stream;
+    if (item >= nitems) break;  // warp-uniform
+    Chunk ch;
+    load_item<8, true>(x, y, n, item, lane, ch);  // the layout does not matter for a maximum
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint64_t a = ch.x[j], b = ch.y[j];
+      const bool ok = ((ch.vmask >> j) & 1u) && !is_zero(a) && !is_zero(b) && !is_nonfinite(a) && !is_nonfinite(b);
+      if (ok) wmax = max(wmax, exponent_of(a) + exponent_of(b) + 2046);
+    }
+  }
+  wmax = __reduce_max_sync(0xffffffffu, wmax);
+  if (lane == 0 && wmax != kNone) atomicMax(erun, wmax);
+}
+
 // Streaming kernel with item records.  LOG2B = 0: blocks of one component,
 // each quantized to the class of its score key - e_lo - f_spec + 1.  LOG2B =
 // 5..8: blocks of 2^LOG2B, each block's components to the class of the block
@@ -587,6 +620,11 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
   const long long gwarp = ((long long)blockIdx.x * kOpThreads + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * kOpThreads) >> 5;
   int e_lo = kNone, pending = kNone, raised = 0, iter = 0;
+  {  // the bound k_seed_bound left: the largest key of every warp's first items
+    int seeded = kNone;
+    if (lane == 0) seeded = *(volatile int*)erun;
+    e_lo = max(kNone, __shfl_sync(0xffffffffu, seeded, 0));
+  }
   extern __shared__ uint4 s_ring[];
   uint4* ring = s_ring + (threadIdx.x >> 5) * (kStages * kStageWords);
 #pragma unroll
@@ -1029,7 +1067,6 @@ cudaError_t launch_items(const double* x, const double* y, int64_t n, const qdot
   if (e != cudaSuccess) return e;
   cudaEvent_t ev0, ev1;
   kernel_events(&ev0, &ev1);
-  if (ev0) cudaEventRecord(ev0, st);
   static bool smem_set = false;
   if (!smem_set) {
     e = cudaFuncSetAttribute(k_onepass_items<LOG2B>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOpSmem);
@@ -1037,6 +1074,8 @@ cudaError_t launch_items(const double* x, const double* y, int64_t n, const qdot
     smem_set = true;
   }
   auto* iblk = LOG2B ? reinterpret_cast<unsigned long long*>(ws + pl.off_slot3) : nullptr;
+  k_seed_bound<<<pl.grid, kOpThreads, 0, st>>>(x, y, n, (long long)pl.grid * kOpWarps, &hdr->erun);
+  if (ev0) cudaEventRecord(ev0, st);  // the streaming kernel alone
   k_onepass_items<LOG2B><<<pl.grid, kOpThreads, kOpSmem, st>>>(x, y, n, f_spec, mh, ms, &hdr->erun, wst, isum,
                                                                  imeta, iblk, tr.cls);
   if (ev1) cudaEventRecord(ev1, st);
@@ -1058,8 +1097,8 @@ bool one_pass_supported(int64_t n, const qdot_params* p, bool aligned16) {
   return aligned16 && n > 0 && (p->block == 1 || (p->block >= 32 && p->block <= 256));
 }
 
-// stream, select, gather (+ the item records' redo)
-int one_pass_launches(int64_t n, const qdot_params* p) { return plan_one_pass(n, p).items ? 4 : 3; }
+// stream, select, gather (+ the item records' seed and redo)
+int one_pass_launches(int64_t n, const qdot_params* p) { return plan_one_pass(n, p).items ? 5 : 3; }
 
 const char* one_pass_stream_kernel(int64_t n, const qdot_params* p) {
   return plan_one_pass(n, p).items ? "k_onepass_items" : "k_onepass";
