@@ -380,7 +380,7 @@ def run_batched(args, rank, world, local, dist, lib):
                               "median_rel_err_vs_exact_dot": statistics.median(rel_vs_exact) if rel_vs_exact else None,
                               "max_rel_err_vs_exact_dot": max(rel_vs_exact) if rel_vs_exact else None},
         "autotune": tuned,
-        "cpu_baseline": None, "e2e": None, "gpu_launches": 3 * args.steps, "clocks": clk,
+        "cpu_baseline": None, "e2e": None, "gpu_launches": (6 if args.block == 32 else 3) * args.steps, "clocks": clk,
     }
 
 

@@ -796,9 +796,9 @@ __device__ __forceinline__ void acc_components_mode(unsigned rmode, const Chunk&
 // 2^(u - 52) (u its largest key, unbiased, in *u_out; kNone if the item has no
 // nonzero component), adds the lane's class counts to c and, when tcls is
 // given (qdot_trace), writes each component's class.
-template <int LOG2B>
+template <int LOG2B, typename Lut = const uint8_t*>
 __device__ long long recompute_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
-                                    long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
+                                    long long item, Lut lut, int lane, int* u_out,
                                     unsigned long long (&c)[5], uint8_t* __restrict__ tcls) {
   constexpr int LB = LOG2B ? LOG2B : 8;  // the item layout (blocks of one: that of 256)
   constexpr int L = Map<LB>::L;
@@ -849,33 +849,44 @@ __device__ long long recompute_item(const double* __restrict__ x, const double* 
   return v;
 }
 
-template <int LOG2B>
+template <int LOG2B, typename Lut = const uint8_t*>
 __device__ long long recompute_loaded_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
-                                           long long item, const Chunk& ch, const uint8_t* __restrict__ lut,
+                                           long long item, const Chunk& ch, Lut lut,
                                            int lane, int* u_out, unsigned long long (&c)[5],
                                            uint8_t* __restrict__ tcls);
+
+// The selection's class table as a formula: entry k (the key kKeyMin + k) has
+// the class of the score kKeyMin + k - e_max - f + 1 (a bin or block key; eq.
+// bin-score-def, eq. precision-def).  Stands in for the 4224-byte table where
+// every item may belong to a different problem.
+struct ClassByAnchor {
+  int e_max, f, mh, ms;
+  __device__ __forceinline__ int operator[](int k) const {
+    return precision_of((long long)kKeyMin + k - e_max - f + 1, mh, ms);
+  }
+};
 
 // recompute_item() on the streaming kernel's arithmetic, for an item whose
 // components are all in range, nonzero, normal and finite: the lanes load it
 // in the streaming layout and quantize with the final classes from the table
 // (per component, or per block from the block key log2 B + u_b).  Any other
 // item goes to recompute_item().
-template <int LOG2B>
+template <int LOG2B, typename Lut = const uint8_t*>
 __device__ long long recompute_item_fast(const double* __restrict__ x, const double* __restrict__ y, long long n,
-                                         long long item, const uint8_t* __restrict__ lut, int lane, int* u_out,
+                                         long long item, Lut lut, int lane, int* u_out,
                                          unsigned long long (&c)[5], uint8_t* __restrict__ tcls) {
   constexpr int LB = LOG2B ? LOG2B : 8;
   Chunk ch;
   load_item<LB>(x, y, n, item, lane, ch);
-  return recompute_loaded_item<LOG2B>(x, y, n, item, ch, lut, lane, u_out, c, tcls);
+  return recompute_loaded_item<LOG2B, Lut>(x, y, n, item, ch, lut, lane, u_out, c, tcls);
 }
 
 // recompute_item_fast() on an item the warp has already loaded (in the
 // streaming layout, `ch`); an item that is not plain goes to recompute_item(),
 // which reads it again.
-template <int LOG2B>
+template <int LOG2B, typename Lut>
 __device__ long long recompute_loaded_item(const double* __restrict__ x, const double* __restrict__ y, long long n,
-                                           long long item, const Chunk& ch, const uint8_t* __restrict__ lut,
+                                           long long item, const Chunk& ch, Lut lut,
                                            int lane, int* u_out, unsigned long long (&c)[5],
                                            uint8_t* __restrict__ tcls) {
   constexpr int LB = LOG2B ? LOG2B : 8;
@@ -883,7 +894,7 @@ __device__ long long recompute_loaded_item(const double* __restrict__ x, const d
   int key[8];
   int cmax = kNone, kmin = INT_MAX;
   if (!__all_sync(0xffffffffu, chunk_keys(ch, key, cmax, kmin)))
-    return recompute_item<LOG2B>(x, y, n, item, lut, lane, u_out, c, tcls);
+    return recompute_item<LOG2B, Lut>(x, y, n, item, lut, lane, u_out, c, tcls);
   const int u = __reduce_max_sync(0xffffffffu, cmax);  // biased
   *u_out = u - 2046;
   double aF = 0.0;

@@ -97,7 +97,41 @@ def test_batched_graph_replay_and_bad_pair(q, orc):
     assert rm[0].count == first[0].count and rm[2].count == first[3].count
 
 
-def test_every_launch_shape_gives_the_same_results(q, orc, tmp_path):
+def test_batched_late_maximum_and_large_pairs(q, orc):
+    """Blocks of 32 (item records per pair): pairs whose largest product sits
+    in their last item, so that most of their items were summed with a stale
+    bound and are taken with changed blocks swapped in or summed again; a pair
+    of 2^20 components split over many warps; many one-item pairs."""
+    import torch
+    rng = np.random.default_rng(8)
+    lengths = [1 << 20, 300000, 65536, 4096, 256, 257] + [int(v) for v in rng.integers(1, 600, 40)]
+    xs, ys = [], []
+    for i, n in enumerate(lengths):
+        x, y = workloads.pair("b", n, 900 + i)
+        if n > 1000 and i % 2 == 0:  # the largest product in the last item
+            x[-2] = np.abs(x).max() * 8.0
+            y[-2] = np.abs(y).max() * 8.0
+        xs.append(x)
+        ys.append(y)
+    bx, xd = _pack(xs)
+    by, yd = _pack(ys)
+    for eps in (1e-15, 1e-8, 1e-1):
+        b = q.Batch(xd, yd, eps=eps, block=32)
+        b.launch()
+        res = b.results()
+        for i, (x, y, r) in enumerate(zip(xs, ys, res)):
+            ref = orc.qdot(x, y, eps=eps, block=32)
+            assert r.status == 0, (i, r)
+            assert r.count == tuple(ref.count), (i, r.count, ref.count)
+            assert (r.e_max, r.e_min, r.n_bins, r.f) == (ref.e_max, ref.e_min, ref.n_bins, ref.f), i
+            assert abs(r.value - ref.value) <= TOL * orc.abs_dot_exact(x, y), (i, r.value, ref.value)
+
+
+@pytest.mark.parametrize("block", [32, 64])
+def test_every_launch_shape_gives_the_same_results(q, orc, tmp_path, block):
+    """Every launch shape the tuner tries gives the same values (blocks of 32:
+    item records, whose speculation depends on the shape but whose values do
+    not; blocks of 64: block records)."""
     import numpy as np
     import torch
     from paper_2105_00115_gb300 import _abi, tune
@@ -107,8 +141,8 @@ def test_every_launch_shape_gives_the_same_results(q, orc, tmp_path):
         x, y = workloads.pair("b", n, 300 + i)
         xs.append(torch.from_numpy(x).cuda())
         ys.append(torch.from_numpy(y).cuda())
-        ref.append(orc.qdot(x, y, eps=1e-8, block=64))
-    batch = q.Batch(xs, ys, eps=1e-8, block=64)
+        ref.append(orc.qdot(x, y, eps=1e-8, block=block))
+    batch = q.Batch(xs, ys, eps=1e-8, block=block)
     seen = set()
     for threads, ctas, staged in tune.CANDIDATES:
         batch.tuning = _abi.BatchedTuning(threads, ctas, 0, staged)
@@ -118,9 +152,9 @@ def test_every_launch_shape_gives_the_same_results(q, orc, tmp_path):
         for r, o, x in zip(res, ref, xs):
             assert r.count == tuple(o.count)
     assert len(seen) == 1  # identical values for every launch shape
-    tuning, times = batch.autotune(reps=2, path=str(tmp_path / "t.json"))
+    tuning, times = batch.autotune(reps=2, path=str(tmp_path / f"t{block}.json"))
     assert (tuning.threads_per_cta, tuning.ctas_per_sm, tuning.staged) in tune.CANDIDATES
     assert len(times) == len(tune.CANDIDATES)
-    tuning2, _ = batch.autotune(reps=2, path=str(tmp_path / "t.json"))  # from the cache
+    tuning2, _ = batch.autotune(reps=2, path=str(tmp_path / f"t{block}.json"))  # from the cache
     assert (tuning2.threads_per_cta, tuning2.ctas_per_sm, tuning2.staged) == \
         (tuning.threads_per_cta, tuning.ctas_per_sm, tuning.staged)
