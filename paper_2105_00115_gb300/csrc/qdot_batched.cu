@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(1024) k_bscan(const PairPart* __restrict__ pp,
 //    k_bfinal_items checked) goes to the pair's sum.
 // 2. Listed items: one per warp, summed whole with the pair's final classes.
 template <int LOG2B>
-__global__ void __launch_bounds__(256) k_bredo(const double* const* __restrict__ xs,
+__global__ void __launch_bounds__(256, 2) k_bredo(const double* const* __restrict__ xs,
                                                const double* const* __restrict__ ys,
                                                const long long* __restrict__ ns, int count,
                                                const long long* __restrict__ gpre,
@@ -622,66 +622,98 @@ __global__ void __launch_bounds__(256) k_bredo(const double* const* __restrict__
     }
     return lo;
   };
-  // 1. listed blocks
+  // 1. listed blocks.  The warp reads the entries of 32 / (32 / BPI)
+  //    iterations with one load (entry base + lane), and loads the next
+  //    iteration's blocks while it sums the current ones.
   {
     const long long nf = fpre[count];
     const long long units = (nf + BPI - 1) / BPI;  // warp iterations
     const long long per = (units + nwarps - 1) / nwarps;
     const long long u0 = gwarp * per, u1 = min(units, u0 + per);
+    constexpr int kIters = 32 / BPI;  // iterations whose entries one warp-wide load covers
     int q = u0 < u1 ? first_pair(fpre, u0 * BPI) : 0;
-    for (long long it = u0; it < u1; ++it) {  // warp-uniform
-      const long long e = it * BPI + g;
-      const bool have = e < nf;
-      int pq = q;
-      if (have) pq = pair_of(fpre, e, q);
-      const unsigned long long E = have ? (unsigned long long)fix[bpre[pq] + (e - fpre[pq])] : 0ull;
-      const long long lb = (long long)(E & ((1ull << 38) - 1));
-      const int u = (int)((E >> 38) & 0xFFFu), elo = (int)((E >> 50) & 0xFFFu);
-      const long long item = lb / BPI;
-      const int gi = (int)(lb % BPI);
+    // lane l: entry e0 + l of the current window, its pair and record word
+    long long wbase = -1;
+    long long wE = 0;
+    int wq = 0;
+    auto window = [&](long long it) {  // warp-uniform: the entries of iterations it .. it + kIters - 1
+      const long long e0 = it * BPI;
+      const long long e = e0 + lane;
+      int ql = q;
+      unsigned long long E = 0;
+      if (e < nf) {
+        ql = pair_of(fpre, e, q);
+        E = (unsigned long long)fix[bpre[ql] + (e - fpre[ql])];
+      }
+      wbase = it;
+      wE = (long long)E;
+      wq = ql;
+      q = __shfl_sync(0xffffffffu, ql, 31);
+    };
+    struct Fetched {
+      bool have;
+      int pq;
+      unsigned long long E;
       Chunk ch;
-      ch.vmask = 0xFFu;
-      if (have) {  // the block lies in a plain item, inside the pair's vectors
-        const double* x = xs[pq];
-        const double* y = ys[pq];
+    };
+    auto fetch = [&](long long it, Fetched& fd) {  // warp-uniform
+      if (it - wbase >= kIters || wbase < 0) window(it);
+      const int src = (int)(it - wbase) * BPI + g;
+      fd.E = (unsigned long long)__shfl_sync(0xffffffffu, wE, src);
+      fd.pq = __shfl_sync(0xffffffffu, wq, src);
+      fd.have = it * BPI + g < nf;
+      fd.ch.vmask = 0xFFu;
+      if (fd.have) {  // the block lies in a plain item, inside the pair's vectors
+        const long long lb = (long long)(fd.E & ((1ull << 38) - 1));
+        const long long item = lb / BPI;
+        const int gi = (int)(lb % BPI);
+        const double* x = xs[fd.pq];
+        const double* y = ys[fd.pq];
         const long long base = item * kItem + item_offset<LOG2B>(gi * L + sub, 0);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const double2 av = __ldcs(reinterpret_cast<const double2*>(x + base + 2 * L * j));
           const double2 bv = __ldcs(reinterpret_cast<const double2*>(y + base + 2 * L * j));
-          ch.x[2 * j] = (uint64_t)__double_as_longlong(av.x);
-          ch.x[2 * j + 1] = (uint64_t)__double_as_longlong(av.y);
-          ch.y[2 * j] = (uint64_t)__double_as_longlong(bv.x);
-          ch.y[2 * j + 1] = (uint64_t)__double_as_longlong(bv.y);
+          fd.ch.x[2 * j] = (uint64_t)__double_as_longlong(av.x);
+          fd.ch.x[2 * j + 1] = (uint64_t)__double_as_longlong(av.y);
+          fd.ch.y[2 * j] = (uint64_t)__double_as_longlong(bv.x);
+          fd.ch.y[2 * j + 1] = (uint64_t)__double_as_longlong(bv.y);
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) ch.x[j] = ch.y[j] = 0ull;
+        for (int j = 0; j < 8; ++j) fd.ch.x[j] = fd.ch.y[j] = 0ull;
       }
+    };
+    Fetched cur, nxt;
+    if (u0 < u1) fetch(u0, cur);
+    for (long long it = u0; it < u1; ++it) {  // warp-uniform
+      if (it + 1 < u1) fetch(it + 1, nxt);
+      const int u = (int)((cur.E >> 38) & 0xFFFu), elo = (int)((cur.E >> 50) & 0xFFFu);
       int key[8];
       int cmax = kNone, kmin = INT_MAX;
-      chunk_keys(ch, key, cmax, kmin);
+      chunk_keys(cur.ch, key, cmax, kmin);
       const int ub = group_max<L>(cmax);  // every lane joins its block's shuffles
       int c_old = kPerf, c_new = kPerf;
       long long d = 0;
-      if (have) {
-        const PairPart& r = pp[pq];
-        c_old = precision_of((long long)LOG2B + ub - (elo + ps[pq].f_spec - 1), mh, ms);
+      if (cur.have) {
+        const PairPart& r = pp[cur.pq];
+        c_old = precision_of((long long)LOG2B + ub - (elo + ps[cur.pq].f_spec - 1), mh, ms);
         c_new = precision_of((long long)LOG2B + ub - (r.e_max + 2046 + r.f - 1), mh, ms);
         const unsigned p_old = c_old == kPerf ? 0u : 1u << c_old, p_new = c_new == kPerf ? 0u : 1u << c_new;
         double h = 0.0, sg = 0.0, a0 = 0.0, a1 = 0.0;
-        acc_lane<LOG2B, 3, 0u>(ch, key, u, p_old, h, sg, a0);
-        acc_lane<LOG2B, 3, 0u>(ch, key, u, p_new, h, sg, a1);
+        acc_lane<LOG2B, 3, 0u>(cur.ch, key, u, p_old, h, sg, a0);
+        acc_lane<LOG2B, 3, 0u>(cur.ch, key, u, p_new, h, sg, a1);
         d = (p_new ? __double2ll_rz(a1 * 4503599627370496.0) : 0ll) -
             (p_old ? __double2ll_rz(a0 * 4503599627370496.0) : 0ll);  // grid 2^(u - 52)
       }
       d = group_sum<L>(d);
-      if (have && sub == 0) {
+      if (cur.have && sub == 0) {
+        const int pq = cur.pq;
         atomic_add_i128(&pp[pq].lo, &pp[pq].hi, candidate_to_fixed(d, kSingle, u - 2046, 8, pp[pq].lsb));
         atomicAdd(&pp[pq].cnt[c_old], (unsigned long long)(-(long long)B));
         atomicAdd(&pp[pq].cnt[c_new], (unsigned long long)B);
       }
-      q = __shfl_sync(0xffffffffu, pq, 31);  // the last group's pair: the next iteration starts there or later
+      cur = nxt;
     }
   }
   // 2. listed items
