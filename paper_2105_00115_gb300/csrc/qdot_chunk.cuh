@@ -776,6 +776,60 @@ __device__ __forceinline__ void acc_components(const Chunk& ch, const int (&key)
   }
 }
 
+// The same rounding for components of any class through one table lookup
+// per component instead of per-class code: the operand bits v become
+// (v + inc + tie) & mask, tie = 1 when v & lsb != 0.  HALF: round to nearest
+// even at bit 42 (inc = 2^41 - 1, mask clears bits 0..41, lsb = bit 42);
+// SINGLE: at bit 29; DOUBLE: the identity; PERF: zero.  These are the bits
+// round_bits<42>, the SINGLE add-and-mask and the PERF zero of
+// acc_components give, so both return the same chain.
+struct RoundTab {
+  uint4 a[4];  // per class: inc low, inc high, mask low, mask high
+  uint2 b[4];  // per class: lsb low, lsb high
+};
+
+// Entry c (0 <= c < 4) of the table.
+__device__ __forceinline__ void round_tab_fill(RoundTab* t, int c) {
+  if (c == kHalf) {
+    t->a[c] = make_uint4(0xFFFFFFFFu, 0x1FFu, 0u, 0xFFFFFC00u);
+    t->b[c] = make_uint2(0u, 1u << 10);
+  } else if (c == kSingle) {
+    t->a[c] = make_uint4(0x0FFFFFFFu, 0u, 0xE0000000u, 0xFFFFFFFFu);
+    t->b[c] = make_uint2(1u << 29, 0u);
+  } else if (c == kDouble) {
+    t->a[c] = make_uint4(0u, 0u, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    t->b[c] = make_uint2(0u, 0u);
+  } else {  // kPerf
+    t->a[c] = make_uint4(0u, 0u, 0u, 0u);
+    t->b[c] = make_uint2(0u, 0u);
+  }
+}
+
+__device__ __forceinline__ uint64_t round_by_tab(uint64_t v, uint4 a, uint2 b) {
+  const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+  const uint32_t tie = min((lo & b.x) | (hi & b.y), 1u);
+  const uint64_t inc = ((uint64_t)a.y << 32) | a.x;
+  const uint64_t mask = ((uint64_t)a.w << 32) | a.z;
+  return (v + inc + tie) & mask;
+}
+
+// acc_components<7> through the table (tab in shared memory).
+__device__ __forceinline__ void acc_components_tab(const Chunk& ch, const int (&key)[8], int u, const int (&cls)[8],
+                                                   const RoundTab* tab, double& aF) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t hx = (uint32_t)(ch.x[j] >> 32), lx = (uint32_t)ch.x[j];
+    const uint32_t hy = (uint32_t)(ch.y[j] >> 32), ly = (uint32_t)ch.y[j];
+    const int d = u - key[j];
+    const uint32_t ye = 0x3FF00000u - (uint32_t)min(d, 1022) * 0x00100000u;  // exponent field 1023 - d
+    const uint4 a = tab->a[cls[j]];
+    const uint2 b = tab->b[cls[j]];
+    const uint64_t xo = round_by_tab(((uint64_t)((hx & 0x800FFFFFu) | 0x3FF00000u) << 32) | lx, a, b);
+    const uint64_t yo = round_by_tab(((uint64_t)((hy & 0x800FFFFFu) | ye) << 32) | ly, a, b);
+    aF = fma(__longlong_as_double((long long)xo), __longlong_as_double((long long)yo), aF);
+  }
+}
+
 __device__ __forceinline__ void acc_components_mode(unsigned rmode, const Chunk& ch, const int (&key)[8], int u,
                                                     const int (&cls)[8], double& aF) {
   switch (rmode) {  // warp-uniform

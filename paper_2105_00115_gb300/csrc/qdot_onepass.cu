@@ -626,6 +626,11 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
     e_lo = max(kNone, __shfl_sync(0xffffffffu, seeded, 0));
   }
   extern __shared__ uint4 s_ring[];
+  __shared__ RoundTab s_rtab;  // blocks of one: the rounding constants per class
+  if (LOG2B == 0) {
+    if (threadIdx.x < 4) round_tab_fill(&s_rtab, threadIdx.x);
+    __syncthreads();
+  }
   uint4* ring = s_ring + (threadIdx.x >> 5) * (kStages * kStageWords);
 #pragma unroll
   for (int st = 0; st < kStages - 1; ++st) {
@@ -658,17 +663,17 @@ __global__ void __launch_bounds__(kOpThreads, kOpCtasPerSm) k_onepass_items(cons
       unsigned cnt = 0;  // per-class counts of the lane's components, 8-bit fields
       if (LOG2B == 0) {
         int cls[8];
-        unsigned seen = 0;  // classes present
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 8; ++j) {  // eq. (precision-def): PERF 0, HALF 1, SINGLE 2, DOUBLE 3
           const int sg = key[j] - a;
-          cls[j] = sg < 0 ? kPerf : (sg < mh ? kHalf : (sg < ms ? kSingle : kDouble));
-          seen |= 1u << cls[j];
+          cls[j] = (sg >= 0) + (sg >= mh) + (sg >= ms);
           cnt += 1u << (cls[j] << 3);
         }
-        seen = __reduce_or_sync(0xffffffffu, seen);
-        const unsigned rmode = ((seen >> kSingle) & 1u) | (((seen >> kHalf) & 1u) << 1) | ((seen & 1u) << 2);
-        acc_components_mode(rmode, cur, key, u, cls, aF);
+        // a class count field is nonzero in the OR over the warp iff some lane has that class
+        if ((__reduce_or_sync(0xffffffffu, cnt) & 0x00FFFFFFu) == 0u)
+          acc_components<0>(cur, key, u, cls, aF);  // every component DOUBLE: nothing to round
+        else
+          acc_components_tab(cur, key, u, cls, &s_rtab, aF);
         if (tcls) {  // check output only (qdot_trace)
 #pragma unroll
           for (int j = 0; j < 8; ++j) tcls[it * kItem + item_offset<LB>(lane, j)] = (uint8_t)cls[j];
