@@ -175,6 +175,47 @@ def test_trace_one_pass_components(q, orc, eps):
             assert np.count_nonzero(units["source"] == SRC["item_recomputed"]) > 0
 
 
+def _boundary_operands(n, seed):
+    """float64 values whose significands sit on the rounding boundaries of
+    both classes (exact HALF and SINGLE ties, one unit above and below them,
+    all-ones fractions that carry into the exponent) or are random, with
+    exponents spread over [-40, 40] so that every class occurs in every warp."""
+    rng = np.random.default_rng(seed)
+    kind = rng.integers(0, 8, n)
+    r10 = rng.integers(0, 1 << 10, n, dtype=np.uint64)
+    r23 = rng.integers(0, 1 << 23, n, dtype=np.uint64)
+    one = np.uint64(1)
+    frac = np.select(
+        [kind == 0, kind == 1, kind == 2, kind == 3, kind == 4, kind == 5, kind == 6],
+        [(r10 << np.uint64(42)) | (one << np.uint64(41)),                                  # HALF tie
+         (r10 << np.uint64(42)) | (one << np.uint64(41)) | one,                             # just above
+         (r10 << np.uint64(42)) | ((one << np.uint64(41)) - one),                           # just below
+         (r23 << np.uint64(29)) | (one << np.uint64(28)),                                   # SINGLE tie
+         (r23 << np.uint64(29)) | (one << np.uint64(28)) | one,
+         (r23 << np.uint64(29)) | ((one << np.uint64(28)) - one),
+         (one << np.uint64(52)) - one],                                                     # all ones: carry
+        rng.integers(0, 1 << 52, n, dtype=np.uint64))
+    expo = (rng.integers(-40, 41, n) + 1023).astype(np.uint64)
+    sign = rng.integers(0, 2, n).astype(np.uint64) << np.uint64(63)
+    return (sign | (expo << np.uint64(52)) | frac).view(np.float64)
+
+
+@pytest.mark.parametrize("eps", [1e-8, 1e-3])
+def test_trace_components_rounding_boundaries(q, orc, eps):
+    """Blocks of one on operands at the rounding boundaries: ties to even,
+    one unit off a tie, and carries out of the significand, for HALF and
+    SINGLE components mixed with PERF and DOUBLE ones in every warp (the
+    streaming kernel's per-class rounding table), on the item path and on
+    the one-launch path for blocks of one."""
+    n = (1 << 24) + 77
+    x, y = _boundary_operands(n, 71), _boundary_operands(n, 72)
+    r, units = check_trace(q, orc, x, y, eps, 1, expect_kernel="k_onepass_items")
+    assert all(c > 0 for c in r.count[:4])  # every class occurs
+    m = (1 << 21) + 77
+    r2, _ = check_trace(q, orc, x[:m], y[:m], eps, 1, path="fused")
+    assert all(c > 0 for c in r2.count[:4])
+
+
 def test_trace_one_pass_items_blocks_of_32(q, orc):
     """k_onepass_items + k_op_gather_items with blocks of 32 (n from 2^25):
     each block classed from its key log2 B + u_b, each item of 256 summed on
