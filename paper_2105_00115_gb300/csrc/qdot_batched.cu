@@ -268,6 +268,12 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream(const double
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kBItemRecompute = 1ull << 63;
 
+struct BPairSlot {
+  const double* x;
+  const double* y;
+  long long n, start, end;  // length and item range [start, end) of the pair
+};
+
 template <int LOG2B, int THREADS>
 __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream_items(
     const double* const* __restrict__ xs, const double* const* __restrict__ ys, const long long* __restrict__ ns,
@@ -308,26 +314,42 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_bstream_items(
 
   extern __shared__ uint4 s_bring[];
   uint4* ring = s_bring + (threadIdx.x >> 5) * (2 * kStageWords);
+  // The pair of the next item to load, in a per-warp shared-memory slot that
+  // lane 0 rewrites when the stream crosses into a later pair: an item reads
+  // it with broadcast shared loads instead of loading the pair's entries of
+  // xs, ys, ns and gpre from global memory (those loads stalled every item;
+  // registers for them would spill).
+  __shared__ BPairSlot s_pair[THREADS / 32];
+  BPairSlot* slot = s_pair + (threadIdx.x >> 5);
   long long gg = g0;
   int p = find_pair(gpre, count, g0);
   // the pair's running bound of e_max: this warp's largest key so far, and
   // every 2 items the pair's shared word (read 2 items before it is used)
   int e_lo = kNone, pending = kNone, piter = 0;
   int f_spec = ps[p].f_spec;
-  issue_item<LOG2B>(xs[p], ys[p], ns[p], gg - gpre[p], lane, ring);
+  if (lane == 0) *slot = BPairSlot{xs[p], ys[p], ns[p], gpre[p], gpre[p + 1]};
+  __syncwarp();
+  long long crem = slot->n - (gg - slot->start) * kItem;  // components of item gg and after it in its pair
+  issue_item<LOG2B>(slot->x, slot->y, slot->n, gg - slot->start, lane, ring);
   cp_async_commit();
   int stage = 0;
   Chunk cur;
   while (gg < g1) {
     const long long ngg = gg + 1;
     int np = p;
-    while (np + 1 < count && ngg >= gpre[np + 1]) ++np;
-    if (ngg < g1) issue_item<LOG2B>(xs[np], ys[np], ns[np], ngg - gpre[np], lane, ring + (stage ^ 1) * kStageWords);
+    if (ngg < g1 && ngg >= slot->end) {  // the next item lies in a later pair (empty pairs have no items)
+      np = p + 1;
+      while (np + 1 < count && ngg >= gpre[np + 1]) ++np;
+      __syncwarp();  // every lane has read the slot
+      if (lane == 0) *slot = BPairSlot{xs[np], ys[np], ns[np], gpre[np], gpre[np + 1]};
+      __syncwarp();
+    }
+    const BPairSlot nx = *slot;
+    if (ngg < g1) issue_item<LOG2B>(nx.x, nx.y, nx.n, ngg - nx.start, lane, ring + (stage ^ 1) * kStageWords);
     cp_async_commit();
     cp_async_wait<1>();  // this lane's copies of item gg have landed
-    const long long nn = ns[p];
-    const long long item = gg - gpre[p];
-    read_item<LOG2B>(ring + stage * kStageWords, nn, item, lane, cur);
+    read_item<LOG2B>(ring + stage * kStageWords, crem, 0, lane, cur);  // item 0 of the rest of its pair
+    crem = nx.n - (ngg - nx.start) * kItem;
     stage ^= 1;
     int key[8];
     int cmax = kNone;
