@@ -151,12 +151,23 @@ def measured_peak_hbm():
         return 6800.0, "of fallback"
 
 
-def kernel_source_hash():
+# The sources each recorded kernel is compiled from (its translation unit and
+# the headers it includes); a change to any other file leaves it as it was.
+KERNEL_SOURCES = {
+    "k_onepass_items": ("csrc/qdot_onepass.cu", "csrc/qdot_chunk.cuh", "csrc/qdot_common.cuh",
+                        "csrc/qdot_internal.h", "../include/qdot.h"),
+}
+
+
+def kernel_source_hash(kernel: str = "k_onepass_items"):
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2105_00115_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    pkg = os.path.join(ROOT, "paper_2105_00115_gb300")
+    files = KERNEL_SOURCES.get(kernel)
+    if files is None:  # unknown kernel: every CUDA source
+        csrc = os.path.join(pkg, "csrc")
+        files = sorted(os.path.join("csrc", f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
+    for rel in files:
+        h.update(open(os.path.normpath(os.path.join(pkg, rel)), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -170,7 +181,7 @@ def recorded_traffic(kernel: str, n: int):
     except (OSError, ValueError):
         return None
     ent = rec.get(kernel)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
+    if not ent or ent.get("source_hash") != kernel_source_hash(kernel):
         return None
     return float(ent["dram_bytes"]) * n / float(ent["n"])
 
