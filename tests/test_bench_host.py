@@ -74,3 +74,31 @@ def test_reference_arm_runs_on_rank_zero_only():
 
     # a rank other than 0 returns at once, without touching the oracle or a GPU
     assert bench.run_reference(Args(), 1, 2) is None
+
+
+def test_recorded_traffic_keyed_on_the_kernels_own_sources(tmp_path, monkeypatch):
+    """profiles/traffic.json holds a kernel's DRAM bytes with a hash of the
+    sources that kernel is compiled from: an edit to another CUDA file keeps
+    the record, an edit to one of its own sources voids it (the bench then
+    reports traffic null)."""
+    import json
+    import shutil
+    bench = _bench()
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "paper_2105_00115_gb300", "csrc"), root / "paper_2105_00115_gb300" / "csrc")
+    shutil.copytree(os.path.join(ROOT, "include"), root / "include")
+    (root / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    h0 = bench.kernel_source_hash("k_onepass_items")
+    rec = {"k_onepass_items": {"dram_bytes": 1000.0, "n": 10, "source_hash": h0}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("k_onepass_items", 40) == 4000.0  # scaled by n
+    assert bench.recorded_traffic("k_bstream", 40) is None  # no record
+    other = root / "paper_2105_00115_gb300" / "csrc" / "qdot_batched.cu"
+    other.write_text(other.read_text() + "\n// edit\n")
+    assert bench.kernel_source_hash("k_onepass_items") == h0
+    assert bench.recorded_traffic("k_onepass_items", 40) == 4000.0
+    own = root / "paper_2105_00115_gb300" / "csrc" / "qdot_chunk.cuh"
+    own.write_text(own.read_text() + "\n// edit\n")
+    assert bench.kernel_source_hash("k_onepass_items") != h0
+    assert bench.recorded_traffic("k_onepass_items", 40) is None
